@@ -1,0 +1,179 @@
+/*
+ * f2v.h -- C ABI of the GB300 Force2Vec epoch engine.
+ *
+ * Force2Vec (Rahman, Sujon, Azad, arXiv:2009.10035) embeds the vertices of an
+ * undirected graph G(V, E) with 0/1 adjacency A (Sec. II-A) into Z in R^{n x d}
+ * by minibatch SGD on the negative-sampling loss of Eq. 2.  Each epoch
+ * (Algorithm 1) visits the vertices in minibatches V_b of b consecutive ids;
+ * for every u in V_b it sums the attractive gradient over its neighbours N(u)
+ * and the repulsive gradient over s negative samples (Algorithm 2), using Z as
+ * it stood when the minibatch began, and then applies z_u -= eta * grad
+ * (Eq. 10).  Two force models are offered:
+ *   F2V_TDIST    t-distribution similarity, Eq. 7; gradients Eq. 8 / Eq. 9
+ *                times the unit vector (z_u - z_x)/t of Sec. III-B.  t^2 is
+ *                floored at 1e-8 in the repulsive term.
+ *   F2V_SIGMOID  sigmoid of the dot product, Eq. 3; gradients Eq. 5 / Eq. 6.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return f2v_status and never abort.  A failure leaves a
+ *     message readable through f2v_last_error (per context) or
+ *     f2v_last_error_global (for f2v_create* before a context exists).
+ *   - A CUDA error inside a context makes it sticky-failed: every later call
+ *     on it returns F2V_ESTATE until f2v_destroy.
+ *   - Host arrays passed in stay owned by the caller and are copied before the
+ *     call returns; device pointers passed in must stay valid only for the
+ *     duration of the call (they are read on the context's stream, which the
+ *     call synchronises unless stated otherwise).
+ *   - Graph: symmetric CSR, int32 row_ptr[n+1] with row_ptr[0] = 0, monotone,
+ *     row_ptr[n] = nnz < 2^31, and int32 col_idx[nnz] in [0, n).  Self-loops
+ *     and duplicate entries are rejected (F2V_EINVAL); symmetry is the
+ *     caller's responsibility (checked only with F2V_FLAG_CHECK_SYMMETRY).
+ *   - Embedding layout: row-major n x d FP32, row u = z_u.
+ *   - Randomness is counter-based Philox4x32-10 keyed by `seed`:
+ *       initial z_u[j] = (Philox(ctr=(u, j, 0xFFFF, 0)).x0 >> 8) * 2^-24 - 0.5
+ *       sample k of u in epoch e = Philox(ctr=(u, e, k, 0)).x0 mod n
+ *     (key = (seed & 0xffffffff, seed >> 32)); a sample equal to u adds no
+ *     force.  Results therefore depend only on the inputs and the epoch
+ *     counter, and runs are bit-reproducible.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef F2V_H
+#define F2V_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct f2v_ctx f2v_ctx;
+
+typedef enum {
+    F2V_OK = 0,
+    F2V_EINVAL = 1,    /* invalid argument or graph */
+    F2V_ENOMEM = 2,    /* device or host allocation failed */
+    F2V_ECUDA = 3,     /* a CUDA call failed (context is now sticky-failed) */
+    F2V_ETIMEOUT = 4,  /* a bounded device-side wait ran out */
+    F2V_ESTATE = 5     /* context already failed, or call not valid now */
+} f2v_status;
+
+typedef enum { F2V_TDIST = 0, F2V_SIGMOID = 1 } f2v_model;
+
+/* Storage of Z.  F2V_FP32: Z in FP32.  F2V_BF16: gathered rows stored in
+   BF16 with an FP32 master copy; forces are accumulated and the update
+   applied in FP32 against the master, and the BF16 rows are re-rounded
+   (round-to-nearest-even) from it after each update. */
+typedef enum { F2V_FP32 = 0, F2V_BF16 = 1 } f2v_precision;
+
+/* Learning-rate schedule (Algorithm 1 gives eta = 0.02 as the initial rate).
+   F2V_LR_CONSTANT: eta_e = lr.  F2V_LR_LINEAR: eta_e = lr * (1 - e / E) for a
+   run of E = total_epochs epochs, e the epoch counter. */
+typedef enum { F2V_LR_CONSTANT = 0, F2V_LR_LINEAR = 1 } f2v_schedule;
+
+/* f2v_create_ex flags */
+#define F2V_FLAG_CHECK_SYMMETRY 0x1u   /* reject a CSR that is not symmetric */
+
+/*
+ * Creates a context for one graph on the current CUDA device: validates and
+ * copies the host CSR (row_ptr[n+1], col_idx[nnz]) to the device, allocates
+ * Z and draws Z0 from `seed` (Sec. III-C, "Initialization").  n >= 1,
+ * 1 <= d <= 1024, 0 <= s <= 65534, 1 <= minibatch, lr > 0 finite.
+ * Epoch counter starts at 0, schedule F2V_LR_CONSTANT, precision FP32, the
+ * legacy default stream.  *out receives the context (NULL on failure).
+ */
+f2v_status f2v_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                      f2v_model model, int32_t s, float lr, int32_t minibatch, uint64_t seed,
+                      f2v_ctx **out);
+
+/* As f2v_create, with a storage precision, flags (F2V_FLAG_*) and the CUDA
+   stream (a cudaStream_t, may be NULL) all later work of the context is
+   issued on. */
+f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                         f2v_model model, int32_t s, float lr, int32_t minibatch,
+                         uint64_t seed, f2v_precision precision, uint32_t flags,
+                         void *stream, f2v_ctx **out);
+
+/* Frees every device and host resource of the context.  NULL is a no-op. */
+void f2v_destroy(f2v_ctx *ctx);
+
+/*
+ * Runs one epoch of Algorithm 1 at the current epoch counter e with
+ * eta_e from the schedule, then increments e.  The work is enqueued on the
+ * context's stream; the call returns without waiting for it (errors of the
+ * enqueued kernels surface on the next synchronising call).
+ */
+f2v_status f2v_epoch(f2v_ctx *ctx);
+
+/* Runs `epochs` consecutive epochs (as f2v_epoch repeated). */
+f2v_status f2v_train(f2v_ctx *ctx, int32_t epochs);
+
+/* Waits for all work of the context; reports any device error. */
+f2v_status f2v_synchronize(f2v_ctx *ctx);
+
+/* Copies Z (n*d FP32, row-major; the FP32 master in the BF16 form) to host
+   memory `out` of `count` floats; count must equal n*d.  Synchronous. */
+f2v_status f2v_get_embedding(f2v_ctx *ctx, float *out, size_t count);
+
+/* As f2v_get_embedding into device memory `dev_out`, enqueued on the
+   context's stream without waiting. */
+f2v_status f2v_get_embedding_device(f2v_ctx *ctx, float *dev_out, size_t count);
+
+/* Replaces Z by the host array `z` (n*d FP32).  In the BF16 form the master
+   takes z and the BF16 rows its rounding.  Synchronous. */
+f2v_status f2v_set_embedding(f2v_ctx *ctx, const float *z, size_t count);
+
+f2v_status f2v_set_lr(f2v_ctx *ctx, float lr);
+f2v_status f2v_set_schedule(f2v_ctx *ctx, f2v_schedule schedule, int32_t total_epochs);
+/* Sets the epoch counter (selects the negative samples and eta of the next
+   epoch); with f2v_set_embedding it resumes a run bit-identically. */
+f2v_status f2v_set_epoch(f2v_ctx *ctx, int32_t epoch);
+f2v_status f2v_get_epoch(const f2v_ctx *ctx, int32_t *epoch);
+
+/* Switches the context to another CUDA stream (a cudaStream_t, may be NULL).
+   Work already enqueued on the old stream is waited for first. */
+f2v_status f2v_set_stream(f2v_ctx *ctx, void *stream);
+
+/*
+ * Link-prediction AUC of the current Z on held-out pairs: pos_pairs[2*npos]
+ * and neg_pairs[2*nneg] are host int32 (u, v) pairs.  Score of a pair:
+ * z_u . z_v (sigmoid model) or -||z_u - z_v||^2 (t model), computed in FP64
+ * from the stored rows on the device; AUC = (#{pos > neg} + #{pos == neg}/2)
+ * / (npos * nneg), with the counts reduced exactly in integers.  Synchronous.
+ */
+f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
+                        const int32_t *neg_pairs, int64_t nneg, double *auc);
+
+/* Negative samples the device draws in epoch `epoch`: out[u*s + k] for all
+   u < n, k < s (count must equal n*s).  For checking; synchronous. */
+f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count);
+
+/* Force pairs of one epoch: nnz + n*s (Sec. III-C complexity: O(md + nsd)). */
+f2v_status f2v_pairs_per_epoch(const f2v_ctx *ctx, int64_t *pairs);
+
+/* Device bytes held by the context. */
+f2v_status f2v_device_bytes(const f2v_ctx *ctx, size_t *bytes);
+
+/* Number of kernels the context has launched so far. */
+f2v_status f2v_launch_count(const f2v_ctx *ctx, int64_t *launches);
+
+/*
+ * Per-launch timing of the force kernel: when enabled, every force-kernel
+ * launch is bracketed by CUDA events on the context's stream.  Reading
+ * (synchronous) returns the number of timed launches and their summed
+ * duration in milliseconds, and resets both.
+ */
+f2v_status f2v_set_kernel_timing(f2v_ctx *ctx, int32_t enable);
+f2v_status f2v_read_kernel_timing(f2v_ctx *ctx, int64_t *launches, double *total_ms);
+
+/* Message of the last failure on this context ("" if none). */
+const char *f2v_last_error(const f2v_ctx *ctx);
+
+/* Message of the last failure of a call that had no context (thread-local). */
+const char *f2v_last_error_global(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* F2V_H */

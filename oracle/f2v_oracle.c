@@ -1,0 +1,397 @@
+/*
+ * f2v_oracle.c -- plain FP64 CPU oracle for Force2Vec's minibatch force
+ * computation and SGD update (Rahman, Sujon, Azad, "Force2Vec: Parallel
+ * force-directed graph embedding", arXiv:2009.10035).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU path computes.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header or constant table with the CUDA library; the two meet only at
+ * the seeded graphs the tests hand to both.
+ *
+ * What each function follows:
+ *   orc_philox4x32_10   Philox4x32-10, the published counter-based generator
+ *                       (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+ *                       two-multiply S-box with a Weyl key schedule.
+ *   orc_init_value      random initial embedding (Sec. III-C, "Initialization
+ *                       and hyper parameters"), uniform in [-0.5, 0.5).
+ *   orc_sample          uniform negative sample for vertex u (Sec. III-C,
+ *                       negative sampling; one set of s samples per vertex as
+ *                       in the complexity paragraph of Sec. III-C).
+ *   attractive_grad,    per-pair gradients: sigmoid model Eq. 5 / Eq. 6,
+ *   repulsive_grad      t-distribution model Eq. 8 / Eq. 9, each times the
+ *                       unit vector of Sec. III-B for the t model.
+ *   orc_grad_minibatch  Algorithm 2 (GradMinibatch).
+ *   orc_train           Algorithm 1 with the update of Eq. 10.
+ *   orc_loss_vertex     Eq. 2 with delta from Eq. 3 (sigmoid) or Eq. 7 (t).
+ *   orc_auc             Mann-Whitney AUC of held-out edges (evaluation).
+ *
+ * Readings of the paper taken here (where it is silent or garbled):
+ *   - Synchronous minibatch SGD (Sec. III-B): every gradient of a minibatch is
+ *     computed from Z as it stood when the minibatch began; the minibatch's
+ *     rows are then updated; the next minibatch sees those updates.
+ *   - Minibatch k holds vertex ids [k*b, min((k+1)*b, n)) in id order.
+ *   - Only z_u for u in the minibatch is updated (Algorithm 1, lines 8-9).
+ *   - Negative sample k of vertex u in epoch e is
+ *       w = Philox(key=(seed lo, seed hi), ctr=(u, e, k, 0)).x0 mod n,
+ *     with no neighbour rejection; w == u contributes nothing.
+ *   - Z0[i][j] = (Philox(key, ctr=(i, j, 0xFFFF, 0)).x0 >> 8) * 2^-24 - 0.5,
+ *     exact in FP32 and FP64.  Sample counters use ctr[2] = k < s <= 0xFFFE,
+ *     so the two streams never meet.
+ *   - t model: t^2 is clamped to at least 1e-8 in the repulsive term only.
+ *   - Learning-rate schedule: constant, or eta_e = eta0 * (1 - e/E) for a
+ *     linearly decayed run of E epochs.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TDIST 0
+#define ORC_SIGMOID 1
+
+#define ORC_T2_FLOOR 1e-8
+
+/* OpenMP thread count used by the parallel loops (n <= 0: leave as is). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                       */
+/* ------------------------------------------------------------------ */
+
+static void philox_round(uint32_t c[4], const uint32_t k[2])
+{
+    const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n1 = lo1;
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    const uint32_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;  /* golden ratio */
+            k[1] += 0xBB67AE85u;  /* sqrt(3) - 1 */
+        }
+        philox_round(c, k);
+    }
+    memcpy(out, c, sizeof c);
+}
+
+static uint32_t philox_x0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t ctr[4] = {c0, c1, c2, c3};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial embedding and negative samples                              */
+/* ------------------------------------------------------------------ */
+
+double orc_init_value(uint64_t seed, uint32_t i, uint32_t j)
+{
+    const uint32_t x = philox_x0(seed, i, j, 0xFFFFu, 0u);
+    return ldexp((double)(x >> 8), -24) - 0.5;
+}
+
+void orc_init_embedding(int64_t n, int32_t d, uint64_t seed, double *Z)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t j = 0; j < d; ++j)
+            Z[i * d + j] = orc_init_value(seed, (uint32_t)i, (uint32_t)j);
+}
+
+uint32_t orc_sample(uint64_t seed, uint32_t u, uint32_t epoch, uint32_t k, uint32_t n)
+{
+    return philox_x0(seed, u, epoch, k, 0u) % n;
+}
+
+void orc_samples(uint64_t seed, int64_t n, int32_t s, int32_t epoch, int32_t *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t u = 0; u < n; ++u)
+        for (int32_t k = 0; k < s; ++k)
+            out[u * s + k] = (int32_t)orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
+                                                 (uint32_t)k, (uint32_t)n);
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-pair gradient terms (added into g)                              */
+/* ------------------------------------------------------------------ */
+
+static double sigma(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+static double dot(const double *a, const double *b, int32_t d)
+{
+    double acc = 0.0;
+    for (int32_t j = 0; j < d; ++j) acc += a[j] * b[j];
+    return acc;
+}
+
+static double dist(const double *a, const double *b, int32_t d)
+{
+    double acc = 0.0;
+    for (int32_t j = 0; j < d; ++j) acc += (a[j] - b[j]) * (a[j] - b[j]);
+    return sqrt(acc);
+}
+
+/* attractive: grad of f_a(u,v) with respect to z_u */
+static void attractive_grad(int model, const double *zu, const double *zv, int32_t d, double *g)
+{
+    if (model == ORC_SIGMOID) {
+        /* Eq. 5: -(1 - sigma(z_u . z_v)) z_v */
+        const double c = -(1.0 - sigma(dot(zu, zv, d)));
+        for (int32_t j = 0; j < d; ++j) g[j] += c * zv[j];
+    } else {
+        /* Eq. 8: 2t / (1 + t^2), times the unit vector (z_u - z_v)/t (Sec. III-B) */
+        const double t = dist(zu, zv, d);
+        if (t == 0.0) return;                 /* the force vanishes with t */
+        const double scal = 2.0 * t / (1.0 + t * t);
+        for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zv[j]) / t;
+    }
+}
+
+/* repulsive: grad of f_r(u,w) with respect to z_u */
+static void repulsive_grad(int model, const double *zu, const double *zw, int32_t d, double *g)
+{
+    if (model == ORC_SIGMOID) {
+        /* Eq. 6: sigma(z_u . z_w) z_w */
+        const double c = sigma(dot(zu, zw, d));
+        for (int32_t j = 0; j < d; ++j) g[j] += c * zw[j];
+    } else {
+        /* Eq. 9: -2 / (t (1 + t^2)), times the unit vector (z_u - z_w)/t,
+           with t^2 floored at 1e-8 */
+        double t = dist(zu, zw, d);
+        double t2 = t * t;
+        if (t2 < ORC_T2_FLOOR) { t2 = ORC_T2_FLOOR; t = sqrt(t2); }
+        const double scal = -2.0 / (t * (1.0 + t2));
+        for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zw[j]) / t;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2: GradMinibatch                                          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * grad[(u - u_begin) * d + j] receives the gradient of vertex u for
+ * u in [u_begin, u_end).  The negative samples of u are either drawn from
+ * Philox (samp_ptr == NULL) or read from samp_idx[samp_ptr[u]..samp_ptr[u+1])
+ * (an injected S(u), used by the tests).  A sample equal to u is skipped.
+ */
+void orc_grad_minibatch(int model, int64_t n, int32_t d,
+                        const int32_t *row_ptr, const int32_t *col_idx,
+                        const double *Z, int64_t u_begin, int64_t u_end,
+                        int32_t s, uint64_t seed, int32_t epoch,
+                        const int64_t *samp_ptr, const int32_t *samp_idx,
+                        double *grad)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t u = u_begin; u < u_end; ++u) {
+        const double *zu = Z + u * d;
+        double ga[d], gr[d];            /* grad f_a(u), grad f_r(u) */
+        memset(ga, 0, sizeof ga);
+        memset(gr, 0, sizeof gr);
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            attractive_grad(model, zu, Z + (int64_t)v * d, d, ga);
+        }
+        if (samp_ptr == NULL) {
+            for (int32_t k = 0; k < s; ++k) {
+                const int64_t w = orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
+                                             (uint32_t)k, (uint32_t)n);
+                if (w == u) continue;
+                repulsive_grad(model, zu, Z + w * d, d, gr);
+            }
+        } else {
+            for (int64_t p = samp_ptr[u]; p < samp_ptr[u + 1]; ++p) {
+                const int64_t w = samp_idx[p];
+                if (w == u) continue;
+                repulsive_grad(model, zu, Z + w * d, d, gr);
+            }
+        }
+        double *gu = grad + (u - u_begin) * d;
+        for (int32_t j = 0; j < d; ++j) gu[j] = ga[j] + gr[j];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1                                                          */
+/* ------------------------------------------------------------------ */
+
+double orc_learning_rate(double lr0, int32_t schedule, int32_t total_epochs, int32_t epoch)
+{
+    if (schedule == 1 && total_epochs > 0)
+        return lr0 * (1.0 - (double)epoch / (double)total_epochs);
+    return lr0;
+}
+
+/*
+ * Runs epochs [start_epoch, start_epoch + epochs) of Algorithm 1 on Z in
+ * place.  max_minibatches < 0 runs every minibatch of each epoch; otherwise
+ * only the first max_minibatches of each epoch (used to time a bounded
+ * sample of a large epoch).  Returns 0, or -1 if memory ran out.
+ */
+int orc_train(int model, int64_t n, int32_t d,
+              const int32_t *row_ptr, const int32_t *col_idx,
+              double *Z, int32_t s, int64_t b, uint64_t seed,
+              double lr0, int32_t schedule, int32_t total_epochs,
+              int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
+              const int64_t *samp_ptr, const int32_t *samp_idx)
+{
+    double *grad = (double *)malloc((size_t)b * (size_t)d * sizeof(double));
+    if (!grad) return -1;
+    for (int32_t e = start_epoch; e < start_epoch + epochs; ++e) {
+        const double eta = orc_learning_rate(lr0, schedule, total_epochs, e);
+        int64_t nmb = 0;
+        for (int64_t u0 = 0; u0 < n; u0 += b) {          /* each minibatch V_b */
+            if (max_minibatches >= 0 && nmb >= max_minibatches) break;
+            ++nmb;
+            const int64_t u1 = (u0 + b < n) ? u0 + b : n;
+            orc_grad_minibatch(model, n, d, row_ptr, col_idx, Z, u0, u1, s, seed, e,
+                               samp_ptr, samp_idx, grad);
+            for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
+                for (int32_t j = 0; j < d; ++j)
+                    Z[u * d + j] = Z[u * d + j] - eta * grad[(u - u0) * d + j];
+        }
+    }
+    free(grad);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Loss (Eq. 2 with Eq. 3 / Eq. 7) and evaluation                       */
+/* ------------------------------------------------------------------ */
+
+/* -log delta(z_u, z_v) for a neighbour v */
+static double attractive_loss(int model, const double *zu, const double *zv, int32_t d)
+{
+    if (model == ORC_SIGMOID) {
+        const double x = dot(zu, zv, d);
+        return log(1.0 + exp(-x));                      /* Eq. 3, first sum */
+    }
+    const double t = dist(zu, zv, d);
+    return log(1.0 + t * t);                            /* Eq. 7, first sum */
+}
+
+/* -log(1 - delta(z_u, z_w)) for a negative sample w */
+static double repulsive_loss(int model, const double *zu, const double *zw, int32_t d)
+{
+    if (model == ORC_SIGMOID) {
+        const double x = dot(zu, zw, d);
+        return -log(exp(-x) / (1.0 + exp(-x)));         /* Eq. 3, second sum */
+    }
+    const double t = dist(zu, zw, d);
+    double t2 = t * t;
+    if (t2 < ORC_T2_FLOOR) t2 = ORC_T2_FLOOR;
+    return -log(t2 / (1.0 + t2));                       /* Eq. 7, second sum */
+}
+
+/* L(u) of Eq. 2 for one vertex, with the same sample rule as orc_grad_minibatch */
+double orc_loss_vertex(int model, int64_t n, int32_t d,
+                       const int32_t *row_ptr, const int32_t *col_idx,
+                       const double *Z, int64_t u, int32_t s, uint64_t seed, int32_t epoch,
+                       const int64_t *samp_ptr, const int32_t *samp_idx)
+{
+    const double *zu = Z + u * d;
+    double L = 0.0;
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+        L += attractive_loss(model, zu, Z + (int64_t)col_idx[e] * d, d);
+    if (samp_ptr == NULL) {
+        for (int32_t k = 0; k < s; ++k) {
+            const int64_t w = orc_sample(seed, (uint32_t)u, (uint32_t)epoch, (uint32_t)k,
+                                         (uint32_t)n);
+            if (w == u) continue;
+            L += repulsive_loss(model, zu, Z + w * d, d);
+        }
+    } else {
+        for (int64_t p = samp_ptr[u]; p < samp_ptr[u + 1]; ++p) {
+            if (samp_idx[p] == u) continue;
+            L += repulsive_loss(model, zu, Z + (int64_t)samp_idx[p] * d, d);
+        }
+    }
+    return L;
+}
+
+/* sum of L(u) over all vertices */
+double orc_loss_total(int model, int64_t n, int32_t d,
+                      const int32_t *row_ptr, const int32_t *col_idx,
+                      const double *Z, int32_t s, uint64_t seed, int32_t epoch,
+                      const int64_t *samp_ptr, const int32_t *samp_idx)
+{
+    double total = 0.0;
+    #pragma omp parallel for reduction(+:total) schedule(dynamic, 64)
+    for (int64_t u = 0; u < n; ++u)
+        total += orc_loss_vertex(model, n, d, row_ptr, col_idx, Z, u, s, seed, epoch,
+                                 samp_ptr, samp_idx);
+    return total;
+}
+
+/*
+ * Link-prediction score of a pair: a larger score means "more likely an
+ * edge".  Sigmoid model: z_u . z_v; t model: -||z_u - z_v||^2 (both monotone
+ * in the model's similarity delta).
+ */
+void orc_scores(int model, int32_t d, const double *Z, const int32_t *pairs, int64_t npairs,
+                double *out)
+{
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < npairs; ++i) {
+        const double *a = Z + (int64_t)pairs[2 * i] * d;
+        const double *b = Z + (int64_t)pairs[2 * i + 1] * d;
+        if (model == ORC_SIGMOID) {
+            out[i] = dot(a, b, d);
+        } else {
+            const double t = dist(a, b, d);
+            out[i] = -(t * t);
+        }
+    }
+}
+
+static int cmp_double(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Mann-Whitney U / (P N): probability that a positive outscores a negative,
+   ties counted one half.  Sorts neg in place. */
+double orc_auc(const double *pos, int64_t npos, double *neg, int64_t nneg)
+{
+    if (npos <= 0 || nneg <= 0) return NAN;
+    qsort(neg, (size_t)nneg, sizeof(double), cmp_double);
+    double twice_u = 0.0;   /* counts are integers; exact in double up to 2^53 */
+    for (int64_t i = 0; i < npos; ++i) {
+        /* lo = #neg < pos[i], hi = #neg <= pos[i] */
+        int64_t lo = 0, hi = nneg;
+        while (lo < hi) { int64_t m = (lo + hi) / 2; if (neg[m] < pos[i]) lo = m + 1; else hi = m; }
+        int64_t lo2 = lo, hi2 = nneg;
+        while (lo2 < hi2) { int64_t m = (lo2 + hi2) / 2; if (neg[m] <= pos[i]) lo2 = m + 1; else hi2 = m; }
+        twice_u += 2.0 * (double)lo + (double)(lo2 - lo);
+    }
+    return twice_u / (2.0 * (double)npos * (double)nneg);
+}
