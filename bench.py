@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: Force2Vec epochs on an R-MAT scale-20 graph, d = 128.
+
+Workload (one "step" = one epoch of Algorithm 1, every minibatch):
+  R-MAT n = 2^20, 16 * 2^20 directed edges (a=.57, b=c=.19), symmetrised,
+  5% of the undirected edges held out (~29.8M CSR entries remain);
+  d = 128 FP32, s = 5 negative samples per vertex, minibatch 4096, lr 0.02
+  linearly decayed, t-distribution force model (sigmoid reported beside it).
+Metric: force-pair updates per second, pairs = nnz + n*s per epoch.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_2009_10035_gb300/csrc/f2v_force.cuh",
+                  "paper_2009_10035_gb300/csrc/f2v_device.cuh",
+                  "paper_2009_10035_gb300/csrc/f2v_force_fp32.cu"]
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scale", type=int, default=20)
+    ap.add_argument("--model", choices=["tdist", "sigmoid"], default="tdist")
+    ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
+    ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
+    ap.add_argument("--skip-extra", action="store_true", help="no second force model")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload_config(g, args, d=128, s=5, b=4096):
+    return {
+        "workload": f"force2vec-epoch rmat-scale{args.scale} holdout5% d{d} s{s} b{b}",
+        "graph": f"R-MAT n=2^{args.scale}, 16*2^{args.scale} directed edges (a=.57,b=c=.19), "
+                 "symmetrised, 5% undirected edges held out",
+        "n": int(g.n), "nnz": int(g.nnz), "d": d, "s": s, "minibatch": b,
+        "force_model": args.model, "lr": "0.02 linearly decayed",
+        "step": "one epoch (all minibatches)",
+        "l2": "inputs larger than L2 (Z 2 x 512 MB FP32 double buffer, CSR 120 MB; L2 129 MB)",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], float(parts[3])))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        loaded = [r for r in rows if r[3] > 200.0] or rows
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None):
+    """Times the FP64 oracle over the first minibatches of epoch 0 until about
+    `budget_s` seconds of work; returns (pairs/s, pairs, minibatches, threads)."""
+    import oracle
+    threads = oracle.set_threads(0)
+    Z = oracle.init_embedding(g.n, d, seed)
+    deg = g.degrees()
+    M = -(-g.n // b)
+    done_mb, pairs, elapsed = 0, 0, 0.0
+    chunk = 4
+    while done_mb < M and elapsed < budget_s and (max_mb is None or done_mb < max_mb):
+        k1 = min(M, done_mb + chunk)
+        u0, u1 = done_mb * b, min(g.n, k1 * b)
+        sub_pairs = int(deg[u0:u1].sum()) + (u1 - u0) * s
+        t0 = time.perf_counter()
+        # run minibatches [done_mb, k1) of epoch 0 on the current Z
+        for k in range(done_mb, k1):
+            a0, a1 = k * b, min(g.n, (k + 1) * b)
+            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0)
+            Z[a0:a1] -= 0.02 * G
+        elapsed += time.perf_counter() - t0
+        pairs += sub_pairs
+        done_mb = k1
+    return pairs / elapsed, pairs, done_mb, threads, elapsed
+
+
+def run_reference(args, g, world, rank):
+    if rank != 0:
+        return
+    model = 0 if args.model == "tdist" else 1
+    import oracle
+    threads = oracle.set_threads(0)
+    d, s, b, seed = 128, 5, 4096, 1
+    Z = oracle.init_embedding(g.n, d, seed)
+    deg = g.degrees()
+    mb_per_step = 4
+    M = -(-g.n // b)
+
+    def step(i):
+        k0 = (i * mb_per_step) % M
+        pairs = 0
+        for k in range(k0, min(M, k0 + mb_per_step)):
+            a0, a1 = k * b, min(g.n, (k + 1) * b)
+            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0)
+            Z[a0:a1] -= 0.02 * G
+            pairs += int(deg[a0:a1].sum()) + (a1 - a0) * s
+        return pairs
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    total = 0
+    for i in range(args.steps):
+        total += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = total / dt
+    sample = (f"{mb_per_step} minibatches of b=4096 per step (about "
+              f"{total // max(args.steps, 1)} pairs), epoch 0, FP64")
+    line = {
+        "impl": "reference", "metric": "force-pair updates/s", "value": value,
+        "unit": "pairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(g, args),
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, g, world, rank, local):
+    import torch
+    from paper_2009_10035_gb300 import f2v
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    d, s, b, seed, lr = 128, 5, 4096, 1, 0.02
+    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    total_epochs = max(20, args.warmup + args.steps)
+
+    def make(m):
+        ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=m, s=s, lr=lr, minibatch=b,
+                          seed=seed, stream=stream)
+        ctx.set_schedule(f2v.LR_LINEAR, total_epochs)
+        return ctx
+
+    ctx = make(model)
+    P = ctx.pairs_per_epoch
+    for _ in range(args.warmup):
+        ctx.epoch()
+    ctx.synchronize()
+
+    # ---- headline: K epochs, CUDA events on the launching stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            ctx.epoch()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count - launches0
+    ms_max = max_over_ranks(ms, world)
+    value = world * P * args.steps / (ms_max / 1e3)
+
+    # ---- dominant kernel: per-launch event timing over K more epochs
+    ctx.set_kernel_timing(True)
+    ctx.read_kernel_timing()
+    for _ in range(args.steps):
+        ctx.epoch()
+    ctx.synchronize()
+    n_timed, kernel_ms = ctx.read_kernel_timing()
+    ctx.set_kernel_timing(False)
+    alg_bytes = P * d * 4 * args.steps            # gathered partner rows x d x 4 B
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    peak, peak_kind = hbm_peak()
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.scale:
+            traffic = tr.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    M = -(-g.n // b)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+                "kernel": "force_kernel<32,4,1,true,float> (fused SDDMM+SpMM+update)",
+                "per_launch": {"algorithmic_bytes": alg_bytes / (args.steps * M),
+                               "avg_duration_us": 1e3 * kernel_ms / max(n_timed, 1),
+                               "launches_timed": n_timed},
+                "kernel_share_of_step": kernel_ms / max(ms * 1.0, 1e-9) if n_timed else None}
+    ctx.close()
+
+    extra = {}
+    if not args.skip_extra:
+        other = f2v.SIGMOID if model == f2v.TDIST else f2v.TDIST
+        c2 = make(other)
+        for _ in range(args.warmup):
+            c2.epoch()
+        c2.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            c2.epoch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1)
+        name = "sigmoid" if other == f2v.SIGMOID else "tdist"
+        extra[name] = {"value": P * args.steps / (ms2 / 1e3), "ms_per_step": ms2 / args.steps}
+        c2.close()
+
+    # ---- end to end through the public API: pinned host CSR in, host Z out
+    e2e = None
+    if not args.skip_e2e:
+        rp = torch.from_numpy(g.row_ptr).pin_memory()
+        ci = torch.from_numpy(g.col_idx).pin_memory()
+        zout = torch.empty((g.n, d), dtype=torch.float32).pin_memory()
+        job_epochs = 20
+        reps = 2
+
+        def job():
+            with f2v.Context(rp.numpy(), ci.numpy(), g.n, d, model=model, s=s, lr=lr,
+                             minibatch=b, seed=seed, stream=stream) as c:
+                c.set_schedule(f2v.LR_LINEAR, job_epochs)
+                c.train(job_epochs)
+                c.embedding_into_host(zout.numpy())
+        job()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            job()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * P * job_epochs * reps / dt, "unit": "pairs/s",
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col_idx.nbytes),
+               "d2h_bytes_per_step": int(g.n * d * 4),
+               "step": f"one {job_epochs}-epoch job: create from pinned host CSR, train, "
+                       "copy Z to pinned host memory",
+               "ms_per_job": 1e3 * dt / reps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {mbs} minibatches (b=4096) of epoch 0, {pairs} pairs, FP64, "
+                         f"{el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "force-pair updates/s", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(g, args),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "pairs_per_step": P, "also": extra,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    from paper_2009_10035_gb300 import graphs
+    g = graphs.config2_graph(scale=args.scale)
+    if args.impl == "reference":
+        run_reference(args, g, world, rank)
+    else:
+        run_ours(args, g, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

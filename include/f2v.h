@@ -99,14 +99,24 @@ void f2v_destroy(f2v_ctx *ctx);
 
 /*
  * Runs one epoch of Algorithm 1 at the current epoch counter e with
- * eta_e from the schedule, then increments e.  The work is enqueued on the
- * context's stream; the call returns without waiting for it (errors of the
- * enqueued kernels surface on the next synchronising call).
+ * eta_e from the schedule, then increments e.  (If minibatches of epoch e
+ * were already run with f2v_run_minibatches, only the remaining ones run.)
+ * The work is enqueued on the context's stream; the call returns without
+ * waiting for it (errors of the enqueued kernels surface on the next
+ * synchronising call).
  */
 f2v_status f2v_epoch(f2v_ctx *ctx);
 
 /* Runs `epochs` consecutive epochs (as f2v_epoch repeated). */
 f2v_status f2v_train(f2v_ctx *ctx, int32_t epochs);
+
+/* Runs the next `count` minibatches (V_b = ids [k*b, min((k+1)*b, n)) for
+   k = 0, 1, ... within each epoch), crossing into the next epoch when one
+   ends.  Every other call sees Z as of the last minibatch run. */
+f2v_status f2v_run_minibatches(f2v_ctx *ctx, int32_t count);
+
+/* Current epoch counter and the index of the next minibatch within it. */
+f2v_status f2v_get_progress(const f2v_ctx *ctx, int32_t *epoch, int32_t *minibatch);
 
 /* Waits for all work of the context; reports any device error. */
 f2v_status f2v_synchronize(f2v_ctx *ctx);
@@ -126,7 +136,8 @@ f2v_status f2v_set_embedding(f2v_ctx *ctx, const float *z, size_t count);
 f2v_status f2v_set_lr(f2v_ctx *ctx, float lr);
 f2v_status f2v_set_schedule(f2v_ctx *ctx, f2v_schedule schedule, int32_t total_epochs);
 /* Sets the epoch counter (selects the negative samples and eta of the next
-   epoch); with f2v_set_embedding it resumes a run bit-identically. */
+   epoch, which starts at its first minibatch from the current Z); with
+   f2v_set_embedding it resumes a run bit-identically. */
 f2v_status f2v_set_epoch(f2v_ctx *ctx, int32_t epoch);
 f2v_status f2v_get_epoch(const f2v_ctx *ctx, int32_t *epoch);
 

@@ -80,6 +80,9 @@ def _load():
         lib.orc_grad_minibatch.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i64, i64,
                                            i32, u64, i32, vp, vp, vp]
         lib.orc_grad_minibatch.restype = None
+        lib.orc_grad_minibatch_abs.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp, i64,
+                                               i64, i32, u64, i32, vp, vp, vp, vp]
+        lib.orc_grad_minibatch_abs.restype = None
         lib.orc_learning_rate.argtypes = [f64, i32, i32, i32]
         lib.orc_learning_rate.restype = f64
         lib.orc_train.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i64, u64,
@@ -167,6 +170,27 @@ def grad_minibatch(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
     lib.orc_grad_minibatch(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), u_begin,
                            u_end, s, seed, epoch, _ptr(sp), _ptr(si), _ptr(g))
     return g
+
+
+def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
+                       injected=None, gather=None):
+    """Algorithm 2 for [u_begin, u_end): returns (grad, grad_abs), where
+    grad_abs sums the absolute values of the per-pair terms element by
+    element (the scale of the rounding error of an FP32 evaluation).  With
+    `gather`, partner rows come from that matrix and only z_u from Z."""
+    lib = _load()
+    row_ptr, col_idx = _csr(row_ptr, col_idx)
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    n, d = Z.shape
+    Zp = None if gather is None else np.ascontiguousarray(gather, dtype=np.float64)
+    assert Zp is None or Zp.shape == Z.shape
+    sp, si = _injected(injected)
+    g = np.zeros((u_end - u_begin, d), dtype=np.float64)
+    ga = np.zeros((u_end - u_begin, d), dtype=np.float64)
+    lib.orc_grad_minibatch_abs(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
+                               None if Zp is None else _ptr(Zp), u_begin, u_end, s, seed,
+                               epoch, _ptr(sp), _ptr(si), _ptr(g), _ptr(ga))
+    return g, ga
 
 
 def learning_rate(lr0: float, schedule: int, total_epochs: int, epoch: int) -> float:

@@ -159,29 +159,65 @@ static double dist(const double *a, const double *b, int32_t d)
     return sqrt(acc);
 }
 
+/*
+ * Error scale of the tests (only when gabs is not NULL): for each pair the
+ * term is c(r) * x_j, where r is a reduced scalar (dot product or squared
+ * distance), c the force coefficient and x the partner row (sigmoid) or the
+ * difference z_u - z_v (t model).  Evaluated in finite precision, r carries
+ * an error proportional to r_abs (the same reduction over absolute values),
+ * so the term's first-order error is proportional to
+ *     (|c| + |dc/dr| * r_abs) * |x_j|,
+ * which is what gabs accumulates.
+ */
+static void add_scale(double *gabs, const double *x, int32_t d, double c, double dc, double r_abs)
+{
+    if (!gabs) return;
+    const double w = fabs(c) + fabs(dc) * r_abs;
+    for (int32_t j = 0; j < d; ++j) gabs[j] += w * fabs(x[j]);
+}
+
+static double dot_abs(const double *a, const double *b, int32_t d)
+{
+    double acc = 0.0;
+    for (int32_t j = 0; j < d; ++j) acc += fabs(a[j] * b[j]);
+    return acc;
+}
+
 /* attractive: grad of f_a(u,v) with respect to z_u */
-static void attractive_grad(int model, const double *zu, const double *zv, int32_t d, double *g)
+static void attractive_grad(int model, const double *zu, const double *zv, int32_t d, double *g,
+                            double *gabs)
 {
     if (model == ORC_SIGMOID) {
         /* Eq. 5: -(1 - sigma(z_u . z_v)) z_v */
-        const double c = -(1.0 - sigma(dot(zu, zv, d)));
+        const double x = dot(zu, zv, d);
+        const double c = -(1.0 - sigma(x));
         for (int32_t j = 0; j < d; ++j) g[j] += c * zv[j];
+        if (gabs) add_scale(gabs, zv, d, c, sigma(x) * (1.0 - sigma(x)), dot_abs(zu, zv, d));
     } else {
         /* Eq. 8: 2t / (1 + t^2), times the unit vector (z_u - z_v)/t (Sec. III-B) */
         const double t = dist(zu, zv, d);
         if (t == 0.0) return;                 /* the force vanishes with t */
         const double scal = 2.0 * t / (1.0 + t * t);
         for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zv[j]) / t;
+        if (gabs) {
+            double df[d];
+            for (int32_t j = 0; j < d; ++j) df[j] = zu[j] - zv[j];
+            const double q = t * t;
+            add_scale(gabs, df, d, 2.0 / (1.0 + q), 2.0 / ((1.0 + q) * (1.0 + q)), q);
+        }
     }
 }
 
 /* repulsive: grad of f_r(u,w) with respect to z_u */
-static void repulsive_grad(int model, const double *zu, const double *zw, int32_t d, double *g)
+static void repulsive_grad(int model, const double *zu, const double *zw, int32_t d, double *g,
+                           double *gabs)
 {
     if (model == ORC_SIGMOID) {
         /* Eq. 6: sigma(z_u . z_w) z_w */
-        const double c = sigma(dot(zu, zw, d));
+        const double x = dot(zu, zw, d);
+        const double c = sigma(x);
         for (int32_t j = 0; j < d; ++j) g[j] += c * zw[j];
+        if (gabs) add_scale(gabs, zw, d, c, sigma(x) * (1.0 - sigma(x)), dot_abs(zu, zw, d));
     } else {
         /* Eq. 9: -2 / (t (1 + t^2)), times the unit vector (z_u - z_w)/t,
            with t^2 floored at 1e-8 */
@@ -190,6 +226,12 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
         if (t2 < ORC_T2_FLOOR) { t2 = ORC_T2_FLOOR; t = sqrt(t2); }
         const double scal = -2.0 / (t * (1.0 + t2));
         for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zw[j]) / t;
+        if (gabs) {
+            double df[d];
+            for (int32_t j = 0; j < d; ++j) df[j] = zu[j] - zw[j];
+            const double dc = 2.0 * (1.0 + 2.0 * t2) / (t2 * t2 * (1.0 + t2) * (1.0 + t2));
+            add_scale(gabs, df, d, 2.0 / (t2 * (1.0 + t2)), dc, t2);
+        }
     }
 }
 
@@ -202,7 +244,51 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
  * u in [u_begin, u_end).  The negative samples of u are either drawn from
  * Philox (samp_ptr == NULL) or read from samp_idx[samp_ptr[u]..samp_ptr[u+1])
  * (an injected S(u), used by the tests).  A sample equal to u is skipped.
+ * If grad_abs is not NULL it receives the sum of the absolute values of the
+ * per-pair terms, element by element.  If Zp is not NULL, partner rows
+ * (neighbours and samples) are read from Zp and only z_u from Z: the
+ * storage form that keeps partner rows in reduced precision beside a full
+ * precision copy of each vertex's own row.
  */
+void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
+                            const int32_t *row_ptr, const int32_t *col_idx,
+                            const double *Z, const double *Zp, int64_t u_begin, int64_t u_end,
+                            int32_t s, uint64_t seed, int32_t epoch,
+                            const int64_t *samp_ptr, const int32_t *samp_idx,
+                            double *grad, double *grad_abs)
+{
+    if (Zp == NULL) Zp = Z;
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t u = u_begin; u < u_end; ++u) {
+        const double *zu = Z + u * d;
+        double ga[d], gr[d];            /* grad f_a(u), grad f_r(u) */
+        double *gabs = grad_abs ? grad_abs + (u - u_begin) * d : NULL;
+        memset(ga, 0, sizeof ga);
+        memset(gr, 0, sizeof gr);
+        if (gabs) memset(gabs, 0, sizeof(double) * (size_t)d);
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            attractive_grad(model, zu, Zp + (int64_t)v * d, d, ga, gabs);
+        }
+        if (samp_ptr == NULL) {
+            for (int32_t k = 0; k < s; ++k) {
+                const int64_t w = orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
+                                             (uint32_t)k, (uint32_t)n);
+                if (w == u) continue;
+                repulsive_grad(model, zu, Zp + w * d, d, gr, gabs);
+            }
+        } else {
+            for (int64_t p = samp_ptr[u]; p < samp_ptr[u + 1]; ++p) {
+                const int64_t w = samp_idx[p];
+                if (w == u) continue;
+                repulsive_grad(model, zu, Zp + w * d, d, gr, gabs);
+            }
+        }
+        double *gu = grad + (u - u_begin) * d;
+        for (int32_t j = 0; j < d; ++j) gu[j] = ga[j] + gr[j];
+    }
+}
+
 void orc_grad_minibatch(int model, int64_t n, int32_t d,
                         const int32_t *row_ptr, const int32_t *col_idx,
                         const double *Z, int64_t u_begin, int64_t u_end,
@@ -210,33 +296,8 @@ void orc_grad_minibatch(int model, int64_t n, int32_t d,
                         const int64_t *samp_ptr, const int32_t *samp_idx,
                         double *grad)
 {
-    #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t u = u_begin; u < u_end; ++u) {
-        const double *zu = Z + u * d;
-        double ga[d], gr[d];            /* grad f_a(u), grad f_r(u) */
-        memset(ga, 0, sizeof ga);
-        memset(gr, 0, sizeof gr);
-        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-            const int32_t v = col_idx[e];
-            attractive_grad(model, zu, Z + (int64_t)v * d, d, ga);
-        }
-        if (samp_ptr == NULL) {
-            for (int32_t k = 0; k < s; ++k) {
-                const int64_t w = orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
-                                             (uint32_t)k, (uint32_t)n);
-                if (w == u) continue;
-                repulsive_grad(model, zu, Z + w * d, d, gr);
-            }
-        } else {
-            for (int64_t p = samp_ptr[u]; p < samp_ptr[u + 1]; ++p) {
-                const int64_t w = samp_idx[p];
-                if (w == u) continue;
-                repulsive_grad(model, zu, Z + w * d, d, gr);
-            }
-        }
-        double *gu = grad + (u - u_begin) * d;
-        for (int32_t j = 0; j < d; ++j) gu[j] = ga[j] + gr[j];
-    }
+    orc_grad_minibatch_abs(model, n, d, row_ptr, col_idx, Z, NULL, u_begin, u_end, s, seed,
+                           epoch, samp_ptr, samp_idx, grad, NULL);
 }
 
 /* ------------------------------------------------------------------ */

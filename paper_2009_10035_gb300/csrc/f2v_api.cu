@@ -1,0 +1,848 @@
+// f2v_api.cu -- host driver and C ABI of libf2v (declared in include/f2v.h).
+//
+// The context owns, on one device: the CSR graph, the pair prefix apair and
+// the item table of every minibatch (built once here, since the graph and
+// the minibatch partition are fixed), two embedding buffers that swap roles
+// every epoch, the FP32 master in the BF16 form, and the scratch of split
+// vertices.  An epoch is one launch of the fused force kernel per minibatch,
+// in order, on the context's stream: the launch boundary is the barrier
+// between minibatch k (whose rows it writes) and k+1 (which reads them).
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "f2v.h"
+#include "f2v_device.cuh"
+#include "f2v_internal.h"
+
+namespace f2v {
+
+Shape choose_shape(int d)
+{
+    switch (d) {
+        case 2: return {1, 2, 1, true};
+        case 4: return {1, 4, 1, true};
+        case 8: return {2, 4, 1, true};
+        case 16: return {4, 4, 1, true};
+        case 32: return {8, 4, 1, true};
+        case 64: return {16, 4, 1, true};
+        case 128: return {32, 4, 1, true};
+        case 256: return {32, 4, 2, true};
+        case 512: return {32, 4, 4, true};
+        case 1024: return {32, 4, 8, true};
+        default: break;
+    }
+    int nv = 1;
+    while (nv * 32 < d) nv *= 2;
+    return {32, 1, nv, false};
+}
+
+int items_pairs(const Shape &sh)
+{
+    return sh.L >= 32 ? 32 : 32;
+}
+
+}  // namespace f2v
+
+using namespace f2v;
+
+// Kernels of the auxiliary entry points (initial embedding, sample dump).
+namespace {
+
+// Z0[i][j] = (Philox(ctr=(i, j, 0xFFFF, 0)).x0 >> 8) * 2^-24 - 0.5, written
+// to both the storage rows and (BF16 form) the FP32 master.  The value is a
+// multiple of 2^-24 in [-0.5, 0.5), so BF16 rounding of it is the only loss.
+template <typename Ts>
+__global__ void init_kernel(Ts *z, float *master, int64_t n, int d, uint32_t k0, uint32_t k1)
+{
+    const int64_t total = n * (int64_t)d;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(t / d), j = (uint32_t)(t % d);
+        const uint32_t x = philox_x0(i, j, 0xFFFFu, 0u, k0, k1);
+        const float v = (float)(x >> 8) * 5.9604644775390625e-8f - 0.5f;   // 2^-24
+        if constexpr (sizeof(Ts) == 2) {
+            z[t] = __float2bfloat16_rn(v);
+            master[t] = v;
+        } else {
+            z[t] = v;
+        }
+    }
+}
+
+__global__ void samples_kernel(int32_t *out, int64_t n, int s, uint32_t epoch, uint32_t k0,
+                               uint32_t k1)
+{
+    const int64_t total = n * (int64_t)s;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = (uint32_t)(t / s), k = (uint32_t)(t % s);
+        out[t] = (int32_t)(philox_x0(u, epoch, k, 0u, k0, k1) % (uint32_t)n);
+    }
+}
+
+template <typename Ts>
+__global__ void round_rows_kernel(Ts *z, const float *master, int64_t total)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        z[t] = __float2bfloat16_rn(master[t]);
+}
+
+thread_local std::string g_last_error;
+
+}  // namespace
+
+// Evaluation entry points live in f2v_eval.cu.
+namespace f2v {
+cudaError_t eval_auc_device(const float *zf, const __nv_bfloat16 *zb, int d, int model,
+                            const int32_t *pos, int64_t npos, const int32_t *neg, int64_t nneg,
+                            cudaStream_t st, double *auc, std::string *err);
+}
+
+struct f2v_ctx {
+    int device = 0;
+    int n = 0, d = 0, ld = 0, s = 0, b = 0;
+    int64_t nnz = 0;
+    int model = 0;
+    f2v_precision precision = F2V_FP32;
+    uint64_t seed = 0;
+    float lr = 0.02f;
+    f2v_schedule schedule = F2V_LR_CONSTANT;
+    int total_epochs = 0;
+    int epoch = 0;
+    cudaStream_t stream = nullptr;
+    Shape shape{};
+    int C = 32;
+
+    // host copies of the schedule of work
+    std::vector<int64_t> h_apair;          // n + 1
+    std::vector<int64_t> mb_item_base;     // M + 1
+    int64_t max_items = 0;
+
+    // device buffers
+    int32_t *row_ptr = nullptr, *col_idx = nullptr, *item_u0 = nullptr, *counter = nullptr;
+    int64_t *apair = nullptr;
+    void *z[2] = {nullptr, nullptr};       // float or bf16 rows
+    float *master = nullptr;
+    int levels = 0;                        // combine-tree levels in use
+    float *slots = nullptr;                // all levels, in order
+    int32_t *unit_cnt = nullptr;
+    int cur = 0;                           // buffer holding Z as of the epoch's start
+    int mb_pos = 0;                        // next minibatch of the current epoch
+    size_t device_bytes = 0;
+
+    int blocks_cap = 0;
+    int64_t launches = 0;
+
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free, ev_pending;   // pairs (start, stop)
+    int64_t timed_launches = 0;
+    double timed_ms = 0.0;
+
+    bool failed = false;
+    std::string err;
+};
+
+namespace {
+
+f2v_status fail(f2v_ctx *c, f2v_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (st == F2V_ECUDA) c->failed = true;
+    } else {
+        g_last_error = buf;
+    }
+    return st;
+}
+
+#define F2V_CUDA(ctx, call)                                                             \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? F2V_ENOMEM : F2V_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define F2V_CHECK_CTX(ctx)                                                   \
+    do {                                                                     \
+        if (!(ctx)) return fail(nullptr, F2V_EINVAL, "null context");        \
+        if ((ctx)->failed) return F2V_ESTATE;                                \
+    } while (0)
+
+size_t elem_size(const f2v_ctx *c) { return c->precision == F2V_BF16 ? 2 : 4; }
+
+f2v_status alloc(f2v_ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, F2V_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->device_bytes += bytes;
+    return F2V_OK;
+}
+
+void release(f2v_ctx *c)
+{
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    void *bufs[] = {c->row_ptr, c->col_idx, c->item_u0, c->counter, c->apair,
+                    c->z[0], c->z[1], c->master};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (c->slots) cudaFree(c->slots);
+    if (c->unit_cnt) cudaFree(c->unit_cnt);
+    for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_pending) cudaEventDestroy(e);
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
+// Host-side validation of the CSR (Sec. II-A: 0/1 adjacency, no self-loops).
+f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                          uint32_t flags)
+{
+    if (!row_ptr) return fail(nullptr, F2V_EINVAL, "row_ptr is NULL");
+    if (row_ptr[0] != 0) return fail(nullptr, F2V_EINVAL, "row_ptr[0] = %d, expected 0", row_ptr[0]);
+    for (int32_t u = 0; u < n; ++u)
+        if (row_ptr[u + 1] < row_ptr[u])
+            return fail(nullptr, F2V_EINVAL, "row_ptr not monotone at row %d", u);
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && !col_idx) return fail(nullptr, F2V_EINVAL, "col_idx is NULL");
+    std::vector<int32_t> stamp((size_t)n, -1);
+    for (int32_t u = 0; u < n; ++u) {
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            if (v < 0 || v >= n)
+                return fail(nullptr, F2V_EINVAL, "col_idx[%d] = %d out of range [0, %d)", e, v, n);
+            if (v == u) return fail(nullptr, F2V_EINVAL, "self-loop at vertex %d", u);
+            if (stamp[(size_t)v] == u)
+                return fail(nullptr, F2V_EINVAL, "duplicate entry (%d, %d)", u, v);
+            stamp[(size_t)v] = u;
+        }
+    }
+    if (flags & F2V_FLAG_CHECK_SYMMETRY) {
+        // count (u, v) against (v, u): transpose counts must match row by row
+        std::vector<int64_t> tcount((size_t)n + 1, 0);
+        for (int64_t e = 0; e < nnz; ++e) tcount[(size_t)col_idx[e] + 1]++;
+        for (int32_t u = 0; u < n; ++u)
+            if (tcount[(size_t)u + 1] != row_ptr[u + 1] - row_ptr[u])
+                return fail(nullptr, F2V_EINVAL, "CSR not symmetric (row %d)", u);
+        for (int32_t u = 0; u < n; ++u) tcount[(size_t)u + 1] += tcount[(size_t)u];
+        std::vector<int32_t> tcol((size_t)nnz);
+        std::vector<int64_t> fill(tcount.begin(), tcount.end() - 1);
+        for (int32_t u = 0; u < n; ++u)
+            for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+                tcol[(size_t)fill[(size_t)col_idx[e]]++] = u;
+        for (int32_t u = 0; u < n; ++u) {
+            std::vector<int32_t> a(col_idx + row_ptr[u], col_idx + row_ptr[u + 1]);
+            std::vector<int32_t> b(tcol.begin() + tcount[(size_t)u],
+                                   tcol.begin() + tcount[(size_t)u + 1]);
+            std::sort(a.begin(), a.end());
+            std::sort(b.begin(), b.end());
+            if (a != b) return fail(nullptr, F2V_EINVAL, "CSR not symmetric (row %d)", u);
+        }
+    }
+    return F2V_OK;
+}
+
+// Builds the pair prefix and the per-minibatch item table on the host.
+// Returns false if a minibatch holds 2^31 pairs or more.
+bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &items)
+{
+    const int n = c->n;
+    c->h_apair.assign((size_t)n + 1, 0);
+    for (int u = 0; u < n; ++u) {
+        int64_t cu = (int64_t)(row_ptr[u + 1] - row_ptr[u]) + c->s;
+        if (cu == 0) cu = 1;     // the empty pair: the row is still carried over
+        c->h_apair[(size_t)u + 1] = c->h_apair[(size_t)u] + cu;
+    }
+    const int M = (n + c->b - 1) / c->b;
+    c->mb_item_base.assign((size_t)M + 1, 0);
+    items.clear();
+    c->max_items = 0;
+    for (int k = 0; k < M; ++k) {
+        const int u0 = k * c->b, u1 = std::min(n, u0 + c->b);
+        const int64_t P0 = c->h_apair[(size_t)u0], P1 = c->h_apair[(size_t)u1];
+        if (P1 - P0 >= (int64_t)INT32_MAX - c->C) return false;
+        const int64_t nit = (P1 - P0 + c->C - 1) / c->C;
+        int u = u0;
+        for (int64_t i = 0; i < nit; ++i) {
+            const int64_t q = P0 + i * c->C;
+            while (c->h_apair[(size_t)u + 1] <= q) ++u;
+            items.push_back(u);
+        }
+        c->mb_item_base[(size_t)k + 1] = c->mb_item_base[(size_t)k] + nit;
+        c->max_items = std::max(c->max_items, nit);
+    }
+    return true;
+}
+
+double lr_for_epoch(const f2v_ctx *c, int e)
+{
+    if (c->schedule == F2V_LR_LINEAR && c->total_epochs > 0)
+        return (double)c->lr * (1.0 - (double)e / (double)c->total_epochs);
+    return (double)c->lr;
+}
+
+cudaError_t launch_init(f2v_ctx *c)
+{
+    const uint32_t k0 = (uint32_t)c->seed, k1 = (uint32_t)(c->seed >> 32);
+    const int64_t total = (int64_t)c->n * c->d;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (c->precision == F2V_BF16)
+        init_kernel<__nv_bfloat16><<<blocks, 256, 0, c->stream>>>(
+            (__nv_bfloat16 *)c->z[c->cur], c->master, c->n, c->d, k0, k1);
+    else
+        init_kernel<float><<<blocks, 256, 0, c->stream>>>((float *)c->z[c->cur], nullptr, c->n,
+                                                          c->d, k0, k1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+f2v_status collect_timing(f2v_ctx *c)
+{
+    for (size_t i = 0; i + 1 < c->ev_pending.size(); i += 2) {
+        F2V_CUDA(c, cudaEventSynchronize(c->ev_pending[i + 1]));
+        float ms = 0.f;
+        F2V_CUDA(c, cudaEventElapsedTime(&ms, c->ev_pending[i], c->ev_pending[i + 1]));
+        c->timed_ms += ms;
+        c->timed_launches++;
+        c->ev_free.push_back(c->ev_pending[i]);
+        c->ev_free.push_back(c->ev_pending[i + 1]);
+    }
+    c->ev_pending.clear();
+    return F2V_OK;
+}
+
+f2v_status get_event(f2v_ctx *c, cudaEvent_t *e)
+{
+    if (!c->ev_free.empty()) {
+        *e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return F2V_OK;
+    }
+    F2V_CUDA(c, cudaEventCreate(e));
+    return F2V_OK;
+}
+
+int num_minibatches(const f2v_ctx *c) { return (c->n + c->b - 1) / c->b; }
+
+// Launches the force kernel of minibatch k of the current epoch.
+f2v_status run_minibatch(f2v_ctx *c, int k)
+{
+    const int e = c->epoch;
+    const float eta = (float)lr_for_epoch(c, e);
+    const int nxt = c->cur ^ 1;
+    const int u0 = k * c->b, u1 = std::min(c->n, u0 + c->b);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        f2v_status st = get_event(c, &e0);
+        if (st == F2V_OK) st = get_event(c, &e1);
+        if (st != F2V_OK) return st;
+        F2V_CUDA(c, cudaEventRecord(e0, c->stream));
+    }
+    cudaError_t err;
+    if (c->precision == F2V_BF16) {
+        ForceArgs<__nv_bfloat16> a{};
+        a.row_ptr = c->row_ptr; a.col_idx = c->col_idx; a.apair = c->apair;
+        a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
+        a.zcur = (const __nv_bfloat16 *)c->z[c->cur];
+        a.znext = (__nv_bfloat16 *)c->z[nxt];
+        a.master = c->master; a.counter = c->counter;
+        a.slots = c->slots; a.unit_cnt = c->unit_cnt; a.units0 = std::max<int64_t>(c->max_items, 1);
+        a.P0 = c->h_apair[(size_t)u0]; a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
+        a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
+        a.mb_begin = u0; a.mb_end = u1;
+        a.n = c->n; a.d = c->d; a.ld = c->ld; a.s = c->s; a.C = c->C;
+        a.epoch = (uint32_t)e; a.key0 = (uint32_t)c->seed; a.key1 = (uint32_t)(c->seed >> 32);
+        a.eta = eta; a.model = c->model;
+        err = launch_force_bf16(c->shape, a, c->blocks_cap, c->stream);
+    } else {
+        ForceArgs<float> a{};
+        a.row_ptr = c->row_ptr; a.col_idx = c->col_idx; a.apair = c->apair;
+        a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
+        a.zcur = (const float *)c->z[c->cur];
+        a.znext = (float *)c->z[nxt];
+        a.master = nullptr; a.counter = c->counter;
+        a.slots = c->slots; a.unit_cnt = c->unit_cnt; a.units0 = std::max<int64_t>(c->max_items, 1);
+        a.P0 = c->h_apair[(size_t)u0]; a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
+        a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
+        a.mb_begin = u0; a.mb_end = u1;
+        a.n = c->n; a.d = c->d; a.ld = c->ld; a.s = c->s; a.C = c->C;
+        a.epoch = (uint32_t)e; a.key0 = (uint32_t)c->seed; a.key1 = (uint32_t)(c->seed >> 32);
+        a.eta = eta; a.model = c->model;
+        err = launch_force_fp32(c->shape, a, c->blocks_cap, c->stream);
+    }
+    c->launches++;
+    if (err != cudaSuccess)
+        return fail(c, F2V_ECUDA, "force kernel launch (epoch %d, minibatch %d): %s", e, k,
+                    cudaGetErrorString(err));
+    if (c->timing) {
+        F2V_CUDA(c, cudaEventRecord(e1, c->stream));
+        c->ev_pending.push_back(e0);
+        c->ev_pending.push_back(e1);
+    }
+    return F2V_OK;
+}
+
+// Advances the minibatch position; at the end of an epoch the buffers swap.
+void advance(f2v_ctx *c)
+{
+    if (++c->mb_pos == num_minibatches(c)) {
+        c->mb_pos = 0;
+        c->cur ^= 1;
+        c->epoch++;
+    }
+}
+
+// Runs the remaining minibatches of the current epoch.
+f2v_status run_epoch(f2v_ctx *c)
+{
+    do {
+        f2v_status st = run_minibatch(c, c->mb_pos);
+        if (st != F2V_OK) return st;
+        advance(c);
+    } while (c->mb_pos != 0);
+    return F2V_OK;
+}
+
+// Mid-epoch, rows [0, mb_pos*b) are current in the next buffer only; copy
+// them into the current buffer so that it holds all of Z.  The remaining
+// minibatches read those rows from the next buffer, so progress is kept.
+f2v_status sync_current(f2v_ctx *c)
+{
+    if (c->mb_pos == 0) return F2V_OK;
+    const size_t rows = std::min<size_t>((size_t)c->mb_pos * c->b, (size_t)c->n);
+    const size_t bytes = rows * (size_t)c->ld * elem_size(c);
+    F2V_CUDA(c, cudaMemcpyAsync(c->z[c->cur], c->z[c->cur ^ 1], bytes, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    return F2V_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        cudaGetDevice(&now);
+        if (prev >= 0 && now != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+f2v_status f2v_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                      f2v_model model, int32_t s, float lr, int32_t minibatch, uint64_t seed,
+                      f2v_ctx **out)
+{
+    return f2v_create_ex(row_ptr, col_idx, n, d, model, s, lr, minibatch, seed, F2V_FP32, 0u,
+                         nullptr, out);
+}
+
+f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                         f2v_model model, int32_t s, float lr, int32_t minibatch,
+                         uint64_t seed, f2v_precision precision, uint32_t flags,
+                         void *stream, f2v_ctx **out)
+{
+    if (!out) return fail(nullptr, F2V_EINVAL, "out is NULL");
+    *out = nullptr;
+    g_last_error.clear();
+    if (n < 1) return fail(nullptr, F2V_EINVAL, "n = %d, must be >= 1", n);
+    if (d < 1 || d > 1024) return fail(nullptr, F2V_EINVAL, "d = %d, must be in [1, 1024]", d);
+    if (s < 0 || s > 65534) return fail(nullptr, F2V_EINVAL, "s = %d, must be in [0, 65534]", s);
+    if (minibatch < 1) return fail(nullptr, F2V_EINVAL, "minibatch = %d, must be >= 1", minibatch);
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(nullptr, F2V_EINVAL, "lr must be finite and > 0");
+    if (model != F2V_TDIST && model != F2V_SIGMOID) return fail(nullptr, F2V_EINVAL, "unknown model %d", (int)model);
+    if (precision != F2V_FP32 && precision != F2V_BF16) return fail(nullptr, F2V_EINVAL, "unknown precision %d", (int)precision);
+    f2v_status st = validate_graph(row_ptr, col_idx, n, flags);
+    if (st != F2V_OK) return st;
+
+    f2v_ctx *c = new (std::nothrow) f2v_ctx();
+    if (!c) return fail(nullptr, F2V_ENOMEM, "host allocation failed");
+    cudaError_t ce = cudaGetDevice(&c->device);
+    if (ce != cudaSuccess) {
+        delete c;
+        return fail(nullptr, F2V_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
+    }
+    c->n = n; c->d = d; c->ld = d; c->s = s; c->b = minibatch; c->model = (int)model;
+    c->precision = precision; c->seed = seed; c->lr = lr;
+    c->stream = (cudaStream_t)stream;
+    c->nnz = row_ptr[n];
+    c->shape = choose_shape(d);
+    c->C = items_pairs(c->shape);
+
+    std::vector<int32_t> items;
+    try {
+        if (!build_schedule(c, row_ptr, items)) {
+            delete c;
+            return fail(nullptr, F2V_EINVAL,
+                        "a minibatch holds 2^31 or more force pairs; use a smaller minibatch");
+        }
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, F2V_ENOMEM, "host allocation failed (schedule)");
+    }
+
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    per_sm = 8;
+    c->blocks_cap = std::max(1, sms * per_sm);
+
+    const size_t es = elem_size(c);
+    const size_t zbytes = (size_t)n * (size_t)c->ld * es;
+    st = F2V_OK;
+    if (st == F2V_OK) st = alloc(c, (void **)&c->row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+    if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx, sizeof(int32_t) * (size_t)c->nnz);
+    if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
+    if (st == F2V_OK) st = alloc(c, (void **)&c->item_u0, sizeof(int32_t) * items.size());
+    if (st == F2V_OK) st = alloc(c, (void **)&c->counter, sizeof(int32_t) * (size_t)n);
+    if (st == F2V_OK) st = alloc(c, &c->z[0], zbytes);
+    if (st == F2V_OK) st = alloc(c, &c->z[1], zbytes);
+    if (st == F2V_OK && precision == F2V_BF16)
+        st = alloc(c, (void **)&c->master, (size_t)n * c->ld * sizeof(float));
+    // combine tree: level l has ceil(max_items / 16^l) units, two slots each
+    // (and, from level 1 on, two arrival counters each)
+    if (st == F2V_OK) {
+        int64_t units = std::max<int64_t>(c->max_items, 1);
+        size_t slot_rows = 0, counters = 0;
+        c->levels = 0;
+        while (true) {
+            slot_rows += 2 * (size_t)units;
+            if (c->levels > 0) counters += 2 * (size_t)units;
+            c->levels++;
+            if (units <= 1 || c->levels == kMaxLevels) break;
+            units = (units + kFan - 1) / kFan;
+        }
+        st = alloc(c, (void **)&c->slots, sizeof(float) * (size_t)c->ld * slot_rows);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->unit_cnt, sizeof(int32_t) * (counters + 1));
+        if (st == F2V_OK &&
+            cudaMemsetAsync(c->unit_cnt, 0, sizeof(int32_t) * (counters + 1), c->stream) != cudaSuccess)
+            st = fail(c, F2V_ECUDA, "memset of combine counters failed");
+    }
+    if (st != F2V_OK) {
+        g_last_error = c->err;
+        release(c);
+        delete c;
+        return st;
+    }
+#define CREATE_CUDA(call)                                                            \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            fail(nullptr, F2V_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));       \
+            release(c);                                                              \
+            delete c;                                                                \
+            return F2V_ECUDA;                                                        \
+        }                                                                            \
+    } while (0)
+    CREATE_CUDA(cudaMemcpyAsync(c->row_ptr, row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+                                cudaMemcpyHostToDevice, c->stream));
+    if (c->nnz)
+        CREATE_CUDA(cudaMemcpyAsync(c->col_idx, col_idx, sizeof(int32_t) * (size_t)c->nnz,
+                                    cudaMemcpyHostToDevice, c->stream));
+    CREATE_CUDA(cudaMemcpyAsync(c->apair, c->h_apair.data(), sizeof(int64_t) * ((size_t)n + 1),
+                                cudaMemcpyHostToDevice, c->stream));
+    if (!items.empty())
+        CREATE_CUDA(cudaMemcpyAsync(c->item_u0, items.data(), sizeof(int32_t) * items.size(),
+                                    cudaMemcpyHostToDevice, c->stream));
+    CREATE_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(int32_t) * (size_t)n, c->stream));
+    CREATE_CUDA(launch_init(c));
+    CREATE_CUDA(cudaStreamSynchronize(c->stream));
+#undef CREATE_CUDA
+    *out = c;
+    return F2V_OK;
+}
+
+void f2v_destroy(f2v_ctx *ctx)
+{
+    if (!ctx) return;
+    if (!ctx->failed) cudaStreamSynchronize(ctx->stream);
+    release(ctx);
+    delete ctx;
+}
+
+f2v_status f2v_epoch(f2v_ctx *ctx)
+{
+    F2V_CHECK_CTX(ctx);
+    DeviceGuard g(ctx->device);
+    return run_epoch(ctx);
+}
+
+f2v_status f2v_train(f2v_ctx *ctx, int32_t epochs)
+{
+    F2V_CHECK_CTX(ctx);
+    if (epochs < 0) return fail(ctx, F2V_EINVAL, "epochs = %d < 0", epochs);
+    DeviceGuard g(ctx->device);
+    for (int32_t i = 0; i < epochs; ++i) {
+        f2v_status st = run_epoch(ctx);
+        if (st != F2V_OK) return st;
+    }
+    return F2V_OK;
+}
+
+f2v_status f2v_run_minibatches(f2v_ctx *ctx, int32_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (count < 0) return fail(ctx, F2V_EINVAL, "count = %d < 0", count);
+    DeviceGuard g(ctx->device);
+    for (int32_t i = 0; i < count; ++i) {
+        f2v_status st = run_minibatch(ctx, ctx->mb_pos);
+        if (st != F2V_OK) return st;
+        advance(ctx);
+    }
+    return F2V_OK;
+}
+
+f2v_status f2v_get_progress(const f2v_ctx *ctx, int32_t *epoch, int32_t *minibatch)
+{
+    if (!ctx || !epoch || !minibatch) return fail(nullptr, F2V_EINVAL, "null argument");
+    *epoch = ctx->epoch;
+    *minibatch = ctx->mb_pos;
+    return F2V_OK;
+}
+
+f2v_status f2v_synchronize(f2v_ctx *ctx)
+{
+    F2V_CHECK_CTX(ctx);
+    DeviceGuard g(ctx->device);
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    F2V_CUDA(ctx, cudaGetLastError());
+    return F2V_OK;
+}
+
+f2v_status f2v_get_embedding(f2v_ctx *ctx, float *out, size_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, F2V_EINVAL, "out is NULL");
+    const size_t want = (size_t)ctx->n * ctx->d;
+    if (count != want) return fail(ctx, F2V_EINVAL, "count = %zu, expected n*d = %zu", count, want);
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    const float *src = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    F2V_CUDA(ctx, cudaMemcpyAsync(out, src, want * sizeof(float), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return F2V_OK;
+}
+
+f2v_status f2v_get_embedding_device(f2v_ctx *ctx, float *dev_out, size_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!dev_out) return fail(ctx, F2V_EINVAL, "dev_out is NULL");
+    const size_t want = (size_t)ctx->n * ctx->d;
+    if (count != want) return fail(ctx, F2V_EINVAL, "count = %zu, expected n*d = %zu", count, want);
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    const float *src = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    F2V_CUDA(ctx, cudaMemcpyAsync(dev_out, src, want * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return F2V_OK;
+}
+
+f2v_status f2v_set_embedding(f2v_ctx *ctx, const float *z, size_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!z) return fail(ctx, F2V_EINVAL, "z is NULL");
+    const size_t want = (size_t)ctx->n * ctx->d;
+    if (count != want) return fail(ctx, F2V_EINVAL, "count = %zu, expected n*d = %zu", count, want);
+    DeviceGuard g(ctx->device);
+    if (ctx->precision == F2V_BF16) {
+        F2V_CUDA(ctx, cudaMemcpyAsync(ctx->master, z, want * sizeof(float), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        const int blocks = (int)std::min<int64_t>(((int64_t)want + 255) / 256, 152 * 16);
+        round_rows_kernel<__nv_bfloat16><<<blocks, 256, 0, ctx->stream>>>(
+            (__nv_bfloat16 *)ctx->z[ctx->cur], ctx->master, (int64_t)want);
+        ctx->launches++;
+        F2V_CUDA(ctx, cudaGetLastError());
+    } else {
+        F2V_CUDA(ctx, cudaMemcpyAsync(ctx->z[ctx->cur], z, want * sizeof(float),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (ctx->mb_pos > 0) {   // mid-epoch: updated rows are read from the next buffer
+        const size_t rows = std::min<size_t>((size_t)ctx->mb_pos * ctx->b, (size_t)ctx->n);
+        F2V_CUDA(ctx, cudaMemcpyAsync(ctx->z[ctx->cur ^ 1], ctx->z[ctx->cur],
+                                      rows * (size_t)ctx->ld * elem_size(ctx),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return F2V_OK;
+}
+
+f2v_status f2v_set_lr(f2v_ctx *ctx, float lr)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!(lr > 0.f) || !std::isfinite(lr)) return fail(ctx, F2V_EINVAL, "lr must be finite and > 0");
+    ctx->lr = lr;
+    return F2V_OK;
+}
+
+f2v_status f2v_set_schedule(f2v_ctx *ctx, f2v_schedule schedule, int32_t total_epochs)
+{
+    F2V_CHECK_CTX(ctx);
+    if (schedule != F2V_LR_CONSTANT && schedule != F2V_LR_LINEAR)
+        return fail(ctx, F2V_EINVAL, "unknown schedule %d", (int)schedule);
+    if (schedule == F2V_LR_LINEAR && total_epochs < 1)
+        return fail(ctx, F2V_EINVAL, "linear schedule needs total_epochs >= 1");
+    ctx->schedule = schedule;
+    ctx->total_epochs = total_epochs;
+    return F2V_OK;
+}
+
+f2v_status f2v_set_epoch(f2v_ctx *ctx, int32_t epoch)
+{
+    F2V_CHECK_CTX(ctx);
+    if (epoch < 0) return fail(ctx, F2V_EINVAL, "epoch = %d < 0", epoch);
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    ctx->mb_pos = 0;
+    ctx->epoch = epoch;
+    return F2V_OK;
+}
+
+f2v_status f2v_get_epoch(const f2v_ctx *ctx, int32_t *epoch)
+{
+    if (!ctx || !epoch) return fail(nullptr, F2V_EINVAL, "null argument");
+    *epoch = ctx->epoch;
+    return F2V_OK;
+}
+
+f2v_status f2v_set_stream(f2v_ctx *ctx, void *stream)
+{
+    F2V_CHECK_CTX(ctx);
+    DeviceGuard g(ctx->device);
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->stream = (cudaStream_t)stream;
+    return F2V_OK;
+}
+
+f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
+                        const int32_t *neg_pairs, int64_t nneg, double *auc)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!auc) return fail(ctx, F2V_EINVAL, "auc is NULL");
+    if (npos < 1 || nneg < 1 || !pos_pairs || !neg_pairs)
+        return fail(ctx, F2V_EINVAL, "need at least one positive and one negative pair");
+    for (int64_t i = 0; i < 2 * npos; ++i)
+        if (pos_pairs[i] < 0 || pos_pairs[i] >= ctx->n)
+            return fail(ctx, F2V_EINVAL, "pos_pairs[%lld] out of range", (long long)i);
+    for (int64_t i = 0; i < 2 * nneg; ++i)
+        if (neg_pairs[i] < 0 || neg_pairs[i] >= ctx->n)
+            return fail(ctx, F2V_EINVAL, "neg_pairs[%lld] out of range", (long long)i);
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    std::string err;
+    const float *zf = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    cudaError_t e = eval_auc_device(zf, nullptr, ctx->d, ctx->model, pos_pairs, npos, neg_pairs,
+                                    nneg, ctx->stream, auc, &err);
+    ctx->launches += 3;
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, F2V_ENOMEM, "eval_auc: %s", err.c_str());
+    if (e != cudaSuccess) return fail(ctx, F2V_ECUDA, "eval_auc: %s", err.c_str());
+    return F2V_OK;
+}
+
+f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, F2V_EINVAL, "out is NULL");
+    if (epoch < 0) return fail(ctx, F2V_EINVAL, "epoch < 0");
+    const size_t want = (size_t)ctx->n * ctx->s;
+    if (count != want) return fail(ctx, F2V_EINVAL, "count = %zu, expected n*s = %zu", count, want);
+    if (want == 0) return F2V_OK;
+    DeviceGuard g(ctx->device);
+    int32_t *dbuf = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&dbuf, want * sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "debug_samples: %s", cudaGetErrorString(e));
+    const int blocks = (int)std::min<int64_t>(((int64_t)want + 255) / 256, 152 * 16);
+    samples_kernel<<<blocks, 256, 0, ctx->stream>>>(dbuf, ctx->n, ctx->s, (uint32_t)epoch,
+                                                     (uint32_t)ctx->seed,
+                                                     (uint32_t)(ctx->seed >> 32));
+    ctx->launches++;
+    F2V_CUDA(ctx, cudaGetLastError());
+    F2V_CUDA(ctx, cudaMemcpyAsync(out, dbuf, want * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    F2V_CUDA(ctx, cudaFreeAsync(dbuf, ctx->stream));
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return F2V_OK;
+}
+
+f2v_status f2v_pairs_per_epoch(const f2v_ctx *ctx, int64_t *pairs)
+{
+    if (!ctx || !pairs) return fail(nullptr, F2V_EINVAL, "null argument");
+    *pairs = ctx->nnz + (int64_t)ctx->n * ctx->s;
+    return F2V_OK;
+}
+
+f2v_status f2v_device_bytes(const f2v_ctx *ctx, size_t *bytes)
+{
+    if (!ctx || !bytes) return fail(nullptr, F2V_EINVAL, "null argument");
+    *bytes = ctx->device_bytes;
+    return F2V_OK;
+}
+
+f2v_status f2v_launch_count(const f2v_ctx *ctx, int64_t *launches)
+{
+    if (!ctx || !launches) return fail(nullptr, F2V_EINVAL, "null argument");
+    *launches = ctx->launches;
+    return F2V_OK;
+}
+
+f2v_status f2v_set_kernel_timing(f2v_ctx *ctx, int32_t enable)
+{
+    F2V_CHECK_CTX(ctx);
+    ctx->timing = enable != 0;
+    return F2V_OK;
+}
+
+f2v_status f2v_read_kernel_timing(f2v_ctx *ctx, int64_t *launches, double *total_ms)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!launches || !total_ms) return fail(ctx, F2V_EINVAL, "null argument");
+    DeviceGuard g(ctx->device);
+    f2v_status st = collect_timing(ctx);
+    if (st != F2V_OK) return st;
+    *launches = ctx->timed_launches;
+    *total_ms = ctx->timed_ms;
+    ctx->timed_launches = 0;
+    ctx->timed_ms = 0.0;
+    return F2V_OK;
+}
+
+const char *f2v_last_error(const f2v_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+const char *f2v_last_error_global(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

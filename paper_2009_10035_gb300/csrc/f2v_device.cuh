@@ -1,0 +1,124 @@
+// f2v_device.cuh -- device helpers of libf2v: the Philox4x32-10 generator,
+// row loads/stores for FP32 and BF16 storage, and small group reductions.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace f2v {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies by
+// 0xD2511F53 and 0xCD9E8D57, with the key advanced by the Weyl increments
+// 0x9E3779B9 and 0xBB67AE85 between rounds.  Returns word 0 of the output.
+__device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t c2,
+                                              uint32_t c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo_a = 0xD2511F53u * c0;
+        const uint32_t hi_b = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t lo_b = 0xCD9E8D57u * c2;
+        c0 = hi_b ^ c1 ^ k0;
+        c1 = lo_b;
+        c2 = hi_a ^ c3 ^ k1;
+        c3 = lo_a;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// Row element loads: VEC consecutive elements starting at p, widened to FP32.
+template <int VEC>
+__device__ __forceinline__ void load_vec(const float *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else if constexpr (VEC == 2) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    } else {
+        x[0] = __ldg(p);
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_vec(const __nv_bfloat16 *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    } else if constexpr (VEC == 2) {
+        const unsigned int t = __ldg(reinterpret_cast<const unsigned int *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
+        x[0] = a.x; x[1] = a.y;
+    } else {
+        x[0] = __bfloat162float(p[0]);
+    }
+}
+
+// Loads through L2 only (for data written by other blocks of the same launch).
+template <int VEC>
+__device__ __forceinline__ void load_vec_cg(const float *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const float4 t = __ldcg(reinterpret_cast<const float4 *>(p));
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else if constexpr (VEC == 2) {
+        const float2 t = __ldcg(reinterpret_cast<const float2 *>(p));
+        x[0] = t.x; x[1] = t.y;
+    } else {
+        x[0] = __ldcg(p);
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_vec(float *p, const float *x)
+{
+    if constexpr (VEC == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else if constexpr (VEC == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    } else {
+        p[0] = x[0];
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void store_vec_cg(float *p, const float *x)
+{
+    if constexpr (VEC == 4) {
+        __stcg(reinterpret_cast<float4 *>(p), make_float4(x[0], x[1], x[2], x[3]));
+    } else if constexpr (VEC == 2) {
+        __stcg(reinterpret_cast<float2 *>(p), make_float2(x[0], x[1]));
+    } else {
+        __stcg(p, x[0]);
+    }
+}
+
+// BF16 stores round to nearest even.
+template <int VEC>
+__device__ __forceinline__ void store_vec(__nv_bfloat16 *p, const float *x)
+{
+    if constexpr (VEC == 4) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(x[0], x[1]);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(x[2], x[3]);
+        uint2 t;
+        t.x = *reinterpret_cast<const unsigned int *>(&a);
+        t.y = *reinterpret_cast<const unsigned int *>(&b);
+        *reinterpret_cast<uint2 *>(p) = t;
+    } else if constexpr (VEC == 2) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(x[0], x[1]);
+        *reinterpret_cast<__nv_bfloat162 *>(p) = a;
+    } else {
+        p[0] = __float2bfloat16_rn(x[0]);
+    }
+}
+
+}  // namespace f2v

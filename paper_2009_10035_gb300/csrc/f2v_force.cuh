@@ -1,0 +1,389 @@
+// f2v_force.cuh -- the fused SDDMM + SpMM force kernel and SGD update of one
+// minibatch (Algorithm 2 followed by lines 8-9 of Algorithm 1, Eq. 10).
+//
+// Work decomposition.  The minibatch's force pairs (neighbours of each u in
+// CSR order, then its s negative samples) form one flat sequence; it is cut
+// into items of C pairs, so every group of lanes gets the same amount of
+// gathering regardless of degree skew (the degree-balanced partition of
+// Sec. III-D, at pair granularity).  A group of L lanes walks its item in
+// tiles of L pairs:
+//   1. decode -- lane t finds the vertex and the partner of pair t of the
+//      tile from a window of L consecutive vertices (pair prefix, row
+//      pointers), reading the partner from col_idx (attractive) or drawing it
+//      with Philox (repulsive);
+//   2. gather -- the group fetches the partner rows, U at a time, each lane
+//      a VEC-wide vector of NV slices (128-bit loads for FP32 rows of d >= 4);
+//   3. force -- the dot product (sigmoid) or squared distance (t model) is
+//      reduced with xor shuffles inside the group, turned into the scalar of
+//      Eq. 5/6 or Eq. 8/9, and the scaled row is accumulated in FP32
+//      registers (the SpMM half);
+//   4. update -- when a vertex's pairs end, z_u - eta * g is written to the
+//      next buffer, directly if the item held all its pairs, else through the
+//      ordered combine tree described in f2v_internal.h.
+// Pair positions inside a launch are 32-bit offsets from the minibatch's
+// first pair.  The own row of the next vertex is fetched while the current
+// one is being summed, since vertices of an item are consecutive ids.
+#pragma once
+
+#include <climits>
+
+#include "f2v_device.cuh"
+#include "f2v_internal.h"
+
+namespace f2v {
+
+constexpr int kBlock = 256;
+constexpr int KIND_NONE = 0;   // no force (self sample, or the empty pair)
+constexpr int KIND_ATTR = 1;   // neighbour: attractive force
+constexpr int KIND_REP = 2;    // negative sample: repulsive force
+constexpr float kT2Floor = 1e-8f;
+
+template <int L, int VEC, int NV>
+struct ShapeTraits {
+    static constexpr int E = VEC * NV;                       // elements per lane
+    static constexpr int U0 = (32 / E) < 1 ? 1 : (32 / E);  // rows in flight
+    static constexpr int U1 = U0 > 8 ? 8 : U0;
+    static constexpr int U = U1 > L ? L : U1;
+};
+
+// Element index of lane `gl`'s slot (i, c).
+template <int L, int VEC>
+__device__ __forceinline__ int elem_index(int gl, int i, int c)
+{
+    return (i * L + gl) * VEC + c;
+}
+
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__device__ __forceinline__ void load_row(const Ts *row, int gl, int d, float *x)
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e0 = elem_index<L, VEC>(gl, i, 0);
+        if (EXACT || e0 < d) {
+            load_vec<VEC>(row + e0, x + i * VEC);
+        } else {
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) x[i * VEC + c] = 0.f;
+        }
+    }
+}
+
+template <int L, int VEC, int NV, bool EXACT>
+__device__ __forceinline__ void load_row_cg(const float *row, int gl, int d, float *x)
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e0 = elem_index<L, VEC>(gl, i, 0);
+        if (EXACT || e0 < d) {
+            load_vec_cg<VEC>(row + e0, x + i * VEC);
+        } else {
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) x[i * VEC + c] = 0.f;
+        }
+    }
+}
+
+template <int L, int VEC, int NV, bool EXACT>
+__device__ __forceinline__ void store_row_cg(float *row, int gl, int d, const float *x)
+{
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e0 = elem_index<L, VEC>(gl, i, 0);
+        if (EXACT || e0 < d) store_vec_cg<VEC>(row + e0, x + i * VEC);
+    }
+}
+
+// Own row of u: the FP32 master in the BF16 form, else the current buffer.
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__device__ __forceinline__ void load_own_row(const ForceArgs<Ts> &a, int u, int gl, float *x)
+{
+    if constexpr (sizeof(Ts) == 2)
+        load_row_cg<L, VEC, NV, EXACT>(a.master + (int64_t)u * a.ld, gl, a.d, x);
+    else
+        load_row<L, VEC, NV, EXACT>(a.zcur + (int64_t)u * a.ld, gl, a.d, x);
+}
+
+// z_u <- z_u - eta * g (Eq. 10) into the next buffer (and the master).
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, int u, int gl,
+                                          const float *zu, const float *g)
+{
+    constexpr int E = VEC * NV;
+    float z[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) z[e] = fmaf(-a.eta, g[e], zu[e]);
+    Ts *dst = a.znext + (int64_t)u * a.ld;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int e0 = elem_index<L, VEC>(gl, i, 0);
+        if (EXACT || e0 < a.d) {
+            store_vec<VEC>(dst + e0, z + i * VEC);
+            if constexpr (sizeof(Ts) == 2)
+                store_vec<VEC>(a.master + (int64_t)u * a.ld + e0, z + i * VEC);
+        }
+    }
+}
+
+// Slot of vertex u (pairs [lb, le) of the minibatch) in level-`lvl` unit j:
+// 2j if u holds the unit's first pair, else 2j+1 (u then holds its last).
+__device__ __forceinline__ int64_t unit_slot(int64_t j, int lb, int64_t unit_pairs)
+{
+    return ((int64_t)lb <= j * unit_pairs) ? 2 * j : 2 * j + 1;
+}
+
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
+{
+    constexpr int G = 32 / L;
+    constexpr int E = VEC * NV;
+    constexpr int U = ShapeTraits<L, VEC, NV>::U;
+    static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
+
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (L - 1);
+    const int grp = lane / L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
+    const int warps = blockDim.x >> 5;
+    const int gid = (blockIdx.x * warps + (threadIdx.x >> 5)) * G + grp;
+    const int ngroups = gridDim.x * warps * G;
+    const bool tdist = (a.model == 0);
+
+    for (int item = gid; item < a.n_items; item += ngroups) {
+        const int q_begin = item * a.C;
+        const int q_end = min(q_begin + a.C, a.Pk);
+        int u = __ldg(&a.item_u0[item]);       // vertex holding pair q_begin
+
+        // own rows: the item's first vertex now, the next one ahead of need
+        int ucur = u;
+        float zu[E], zn[E], g[E];
+        load_own_row<L, VEC, NV, EXACT>(a, ucur, gl, zu);
+        if (ucur + 1 < a.mb_end) load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = 0.f;
+        int vbeg = 0, vend = 0;
+
+        // decoded tile (lane gl <-> pair q + gl)
+        int q = q_begin - L;
+        int r = 0, ntile = 0, next_u = u;
+        int pu = u, nb = u, kind = KIND_NONE, pA_hi = 0;
+        for (;;) {
+            if (r == ntile) {
+                // ---- 1. decode the next tile -------------------------------
+                q += L;
+                u = next_u;
+                if (q < q_end) {
+                    const int uu = u + gl;
+                    int A_hi = INT_MAX;
+                    int rp_lo = 0, rp_hi = 0;
+                    if (uu < a.n) {
+                        const int64_t ah = __ldg(&a.apair[uu + 1]) - a.P0;
+                        A_hi = ah > INT_MAX ? INT_MAX : (int)ah;
+                        rp_lo = __ldg(&a.row_ptr[uu]);
+                        rp_hi = __ldg(&a.row_ptr[uu + 1]);
+                    }
+                    const int A_up = __shfl_up_sync(gmask, A_hi, 1, L);
+                    const int A_lo = (gl == 0) ? (int)(__ldg(&a.apair[u]) - a.P0) : A_up;
+                    const int pos = A_hi - q;             // >= 1: vertex uu ends after q
+                    const unsigned bit = (pos < L) ? (1u << pos) : 0u;
+                    const unsigned ends = __reduce_or_sync(gmask, bit);
+                    const int off = __popc(ends & ((2u << gl) - 1u));
+                    pu = u + off;                         // vertex of this lane's pair
+                    const int pA_lo = __shfl_sync(gmask, A_lo, off, L);
+                    pA_hi = __shfl_sync(gmask, A_hi, off, L);
+                    const int prp_lo = __shfl_sync(gmask, rp_lo, off, L);
+                    const int prp_hi = __shfl_sync(gmask, rp_hi, off, L);
+                    nb = pu;
+                    kind = KIND_NONE;
+                    if (q + gl < q_end) {
+                        const int j = q + gl - pA_lo;
+                        const int deg = prp_hi - prp_lo;
+                        if (j < deg) {
+                            nb = __ldg(&a.col_idx[prp_lo + j]);
+                            kind = KIND_ATTR;
+                        } else if (j - deg < a.s) {
+                            const uint32_t x0 = philox_x0((uint32_t)pu, a.epoch,
+                                                          (uint32_t)(j - deg), 0u, a.key0, a.key1);
+                            nb = (int)(x0 % (uint32_t)a.n);
+                            kind = (nb == pu) ? KIND_NONE : KIND_REP;
+                        }
+                    }
+                    if (q == q_begin) {
+                        vbeg = __shfl_sync(gmask, A_lo, 0, L);
+                        vend = __shfl_sync(gmask, A_hi, 0, L);
+                    }
+                    next_u = u + __popc(__ballot_sync(gmask, pos <= L) & gmask);
+                    ntile = min(L, q_end - q);
+                    r = 0;
+                }
+            }
+            // vertex of the next pair; -1 once the item is done
+            const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
+            if (w != ucur) {
+                // ---- 4. update: the only place a vertex is finished ------
+                int64_t fu = vbeg / a.C, lu = (vend - 1) / a.C;
+                if (fu == lu) {
+                    write_row<L, VEC, NV, EXACT>(a, ucur, gl, zu, g);
+                } else {
+                    // pass the part up the ordered combine tree
+                    int64_t unit = item, unit_pairs = a.C, units = a.units0;
+                    float *slot_base = a.slots;
+                    int32_t *cnt_base = a.unit_cnt;
+                    for (int lvl = 0; lvl + 1 < kMaxLevels; ++lvl) {
+                        store_row_cg<L, VEC, NV, EXACT>(
+                            slot_base + unit_slot(unit, vbeg, unit_pairs) * a.ld, gl, a.d, g);
+                        __threadfence();
+                        __syncwarp(gmask);
+                        const int64_t parent = unit / kFan;
+                        const int64_t pfu = fu / kFan, plu = lu / kFan;
+                        const int64_t c0 = max(fu, parent * kFan);
+                        const int64_t c1 = min(lu, parent * kFan + (kFan - 1));
+                        const bool top = (pfu == plu);
+                        const int64_t punits = (units + kFan - 1) / kFan;
+                        int32_t *cnt = top ? &a.counter[ucur]
+                                           : &cnt_base[unit_slot(parent, vbeg, unit_pairs * kFan)];
+                        int prior = 0;
+                        if (gl == 0) prior = atomicAdd(cnt, 1);
+                        prior = __shfl_sync(gmask, prior, 0, L);
+                        if (prior != (int)(c1 - c0)) break;   // a sibling completes it
+                        __threadfence();
+#pragma unroll
+                        for (int e = 0; e < E; ++e) g[e] = 0.f;
+                        for (int64_t c = c0; c <= c1; c += 4) {    // children in order
+                            float part[4][E];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (c + k <= c1)
+                                    load_row_cg<L, VEC, NV, EXACT>(
+                                        slot_base + unit_slot(c + k, vbeg, unit_pairs) * a.ld, gl,
+                                        a.d, part[k]);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (c + k <= c1) {
+#pragma unroll
+                                    for (int e = 0; e < E; ++e) g[e] += part[k][e];
+                                }
+                        }
+                        if (gl == 0) *cnt = 0;
+                        if (top) {
+                            write_row<L, VEC, NV, EXACT>(a, ucur, gl, zu, g);
+                            break;
+                        }
+                        slot_base += 2 * units * a.ld;
+                        cnt_base += 2 * punits;
+                        unit = parent;
+                        fu = pfu;
+                        lu = plu;
+                        units = punits;
+                        unit_pairs *= kFan;
+                    }
+                }
+                if (w < 0) break;
+                // next vertex: always ucur + 1, its own row already fetched
+                ucur = w;
+                vbeg = vend;
+                vend = __shfl_sync(gmask, pA_hi, r, L);
+#pragma unroll
+                for (int e = 0; e < E; ++e) { zu[e] = zn[e]; g[e] = 0.f; }
+                if (ucur + 1 < a.mb_end && vend < q_end)
+                    load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
+            }
+            // ---- 2-3. gather and accumulate this vertex's pairs of the tile
+            const int seg_end = min(ntile, vend - q);
+            for (int r0 = r; r0 < seg_end; r0 += U) {
+                float zv[U][E];
+                int kr[U];
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    const int ri = min(r0 + i, L - 1);
+                    const int v = __shfl_sync(gmask, nb, ri, L);
+                    kr[i] = __shfl_sync(gmask, kind, ri, L);
+                    if (r0 + i >= seg_end) kr[i] = KIND_NONE;
+                    if (kr[i] != KIND_NONE) {
+                        const Ts *src = (v < a.mb_begin) ? a.znext : a.zcur;
+                        load_row<L, VEC, NV, EXACT>(src + (int64_t)v * a.ld, gl, a.d, zv[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < U; ++i) {
+                    if (kr[i] == KIND_NONE) continue;
+                    float part = 0.f;
+                    if (tdist) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            const float df = zu[e] - zv[i][e];
+                            part = fmaf(df, df, part);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
+                    }
+#pragma unroll
+                    for (int m = L / 2; m >= 1; m >>= 1)
+                        part += __shfl_xor_sync(gmask, part, m, L);
+                    if (tdist) {
+                        float coef;
+                        if (kr[i] == KIND_ATTR) {
+                            coef = 2.f / (1.f + part);                 // Eq. 8 / t
+                        } else {
+                            const float q2 = fmaxf(part, kT2Floor);
+                            coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
+                    } else {
+                        const float coef = (kr[i] == KIND_ATTR)
+                                               ? -1.f / (1.f + expf(part))    // Eq. 5
+                                               : 1.f / (1.f + expf(-part));   // Eq. 6
+#pragma unroll
+                        for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
+                    }
+                }
+            }
+            r = seg_end;
+        }
+    }
+}
+
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+cudaError_t launch_shape(const ForceArgs<Ts> &a, int blocks_cap, cudaStream_t st)
+{
+    constexpr int G = 32 / L;
+    const int64_t groups_per_block = (kBlock / 32) * G;
+    int64_t blocks = (a.n_items + groups_per_block - 1) / groups_per_block;
+    if (blocks_cap > 0 && blocks > blocks_cap) blocks = blocks_cap;
+    if (blocks < 1) blocks = 1;
+    force_kernel<L, VEC, NV, EXACT, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Ts>
+cudaError_t launch_force_any(const Shape &sh, const ForceArgs<Ts> &a, int blocks_cap,
+                             cudaStream_t st)
+{
+    if (sh.exact) {
+        switch (sh.L * 100 + sh.VEC * 10 + sh.NV) {
+            case 121: return launch_shape<1, 2, 1, true>(a, blocks_cap, st);
+            case 141: return launch_shape<1, 4, 1, true>(a, blocks_cap, st);
+            case 241: return launch_shape<2, 4, 1, true>(a, blocks_cap, st);
+            case 441: return launch_shape<4, 4, 1, true>(a, blocks_cap, st);
+            case 841: return launch_shape<8, 4, 1, true>(a, blocks_cap, st);
+            case 1641: return launch_shape<16, 4, 1, true>(a, blocks_cap, st);
+            case 3241: return launch_shape<32, 4, 1, true>(a, blocks_cap, st);
+            case 3242: return launch_shape<32, 4, 2, true>(a, blocks_cap, st);
+            case 3244: return launch_shape<32, 4, 4, true>(a, blocks_cap, st);
+            case 3248: return launch_shape<32, 4, 8, true>(a, blocks_cap, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (sh.NV) {
+        case 1: return launch_shape<32, 1, 1, false>(a, blocks_cap, st);
+        case 2: return launch_shape<32, 1, 2, false>(a, blocks_cap, st);
+        case 4: return launch_shape<32, 1, 4, false>(a, blocks_cap, st);
+        case 8: return launch_shape<32, 1, 8, false>(a, blocks_cap, st);
+        case 16: return launch_shape<32, 1, 16, false>(a, blocks_cap, st);
+        case 32: return launch_shape<32, 1, 32, false>(a, blocks_cap, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace f2v

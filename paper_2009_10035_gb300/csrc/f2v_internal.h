@@ -1,0 +1,86 @@
+// f2v_internal.h -- declarations shared by the translation units of libf2v
+// (host driver, force kernels, auxiliary kernels).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace f2v {
+
+// Arguments of one launch of the fused force+update kernel: the work of one
+// minibatch V_b = [mb_begin, mb_end) of Algorithm 1.
+//
+// Pair space.  Vertex u owns c(u) = deg(u) + s force pairs (plus one empty
+// pair when deg(u) + s == 0, so that every vertex is visited and its row is
+// carried into the next buffer).  apair[u] is the exclusive prefix sum of
+// c(u); pair apair[u] + j of u is its j-th neighbour for j < deg(u) and its
+// negative sample k = j - deg(u) otherwise.  The minibatch's pairs
+// [P0, P1) are cut into items of C consecutive pairs; item i starts inside
+// vertex item_u0[i].
+//
+// Double buffering.  zcur holds every row as it stood before this epoch;
+// znext receives the new rows.  Within epoch e, minibatch k reads row v from
+// znext if v < mb_begin (already updated this epoch) and from zcur otherwise
+// (not yet updated, including the minibatch's own rows -- the synchronous
+// minibatch rule of Sec. III-B).  Nothing is copied back: the buffers swap
+// roles at the end of the epoch.
+//
+// Split vertices.  A vertex whose pairs span several items is summed in
+// parts, combined up a fixed tree whose level-l units are runs of 16^l
+// consecutive items.  At each level a split vertex meets a unit either at
+// the unit's first pair or at its last one, so it owns slot 2*unit or
+// 2*unit+1 of that level (`slots`, `unit_cnt`).  The part of the last child
+// to arrive (arrival counter) adds the children's parts in unit order and
+// passes the sum up; at the level where one unit covers the whole vertex the
+// sum is the gradient, and that final arrival counts on counter[u].  Every
+// counter is reset to zero by the part that completes it.  The order of
+// every addition is fixed, so results do not depend on scheduling.
+constexpr int kFan = 16;        // tree fan-out
+constexpr int kMaxLevels = 8;   // 16^8 items per minibatch at most
+
+template <typename Ts>
+struct ForceArgs {
+    const int32_t *row_ptr;    // n + 1
+    const int32_t *col_idx;    // nnz
+    const int64_t *apair;      // n + 1
+    const int32_t *item_u0;    // items of this minibatch
+    const Ts *zcur;            // n x ld
+    Ts *znext;                 // n x ld
+    float *master;             // BF16 form: FP32 master rows (n x ld); else nullptr
+    float *slots;              // level l: 2 * units_l rows of ld floats, levels in order
+    int32_t *unit_cnt;         // level l >= 1: 2 * units_l arrival counters, in order
+    int64_t units0;            // units of level 0 (the most items of any minibatch)
+    int32_t *counter;          // n final arrival counters, zero outside a launch
+    int64_t P0;                // first pair of the minibatch
+    int32_t Pk;                // pairs in the minibatch (< 2^31)
+    int32_t n_items;
+    int32_t mb_begin, mb_end;
+    int32_t n, d, ld, s;
+    int32_t C;                 // pairs per item
+    uint32_t epoch;
+    uint32_t key0, key1;       // Philox key = (seed lo, seed hi)
+    float eta;
+    int32_t model;             // 0 = t-distribution, 1 = sigmoid
+};
+
+// Kernel shape chosen from d: a group of L lanes owns one force pair at a
+// time; each lane holds NV vectors of VEC consecutive elements of a row.
+struct Shape {
+    int L, VEC, NV;
+    bool exact;                // L * VEC * NV == d (else masked generic shape)
+};
+
+Shape choose_shape(int d);
+
+// Pairs per item for a shape.
+int items_pairs(const Shape &sh);
+
+// Launches the force kernel for one minibatch.  Returns the CUDA error of the
+// launch.  `blocks_cap` bounds the grid (0 = no bound).
+cudaError_t launch_force_fp32(const Shape &sh, const ForceArgs<float> &a, int blocks_cap,
+                              cudaStream_t st);
+cudaError_t launch_force_bf16(const Shape &sh, const ForceArgs<__nv_bfloat16> &a,
+                              int blocks_cap, cudaStream_t st);
+
+}  // namespace f2v

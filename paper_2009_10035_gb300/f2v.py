@@ -1,0 +1,259 @@
+"""Python binding of libf2v (the C ABI in include/f2v.h).
+
+Argument marshalling only: every step of an epoch runs in the library's CUDA
+kernels.  If the library has not been built this module raises on first use;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+TDIST = 0
+SIGMOID = 1
+FP32 = 0
+BF16 = 1
+LR_CONSTANT = 0
+LR_LINEAR = 1
+FLAG_CHECK_SYMMETRY = 0x1
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
+_STATUS = {0: "F2V_OK", 1: "F2V_EINVAL", 2: "F2V_ENOMEM", 3: "F2V_ECUDA",
+           4: "F2V_ETIMEOUT", 5: "F2V_ESTATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libf2v.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "f2v.h")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class F2VError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def header_functions() -> list[str]:
+    """Names of the functions include/f2v.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(f2v_[a-z0-9_]+)\s*\(", text)))
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Loads libf2v.so and declares its signatures (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libf2v.so is not built ({p}); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(p)
+        i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+        vp, sz, f32, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sigs = {
+            "f2v_create": ([vp, vp, i32, i32, st, i32, f32, i32, u64, pp], st),
+            "f2v_create_ex": ([vp, vp, i32, i32, st, i32, f32, i32, u64, st, u32, vp, pp], st),
+            "f2v_destroy": ([vp], None),
+            "f2v_epoch": ([vp], st),
+            "f2v_train": ([vp, i32], st),
+            "f2v_run_minibatches": ([vp, i32], st),
+            "f2v_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "f2v_synchronize": ([vp], st),
+            "f2v_get_embedding": ([vp, vp, sz], st),
+            "f2v_get_embedding_device": ([vp, vp, sz], st),
+            "f2v_set_embedding": ([vp, vp, sz], st),
+            "f2v_set_lr": ([vp, f32], st),
+            "f2v_set_schedule": ([vp, st, i32], st),
+            "f2v_set_epoch": ([vp, i32], st),
+            "f2v_get_epoch": ([vp, ctypes.POINTER(i32)], st),
+            "f2v_set_stream": ([vp, vp], st),
+            "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
+            "f2v_debug_samples": ([vp, i32, vp, sz], st),
+            "f2v_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+            "f2v_device_bytes": ([vp, ctypes.POINTER(sz)], st),
+            "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
+            "f2v_set_kernel_timing": ([vp, i32], st),
+            "f2v_read_kernel_timing": ([vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)], st),
+            "f2v_last_error": ([vp], ctypes.c_char_p),
+            "f2v_last_error_global": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)       # a torch.cuda.Stream
+
+
+class Context:
+    """One embedding job: a graph, its device-resident Z and the epoch counter."""
+
+    def __init__(self, row_ptr, col_idx, n: int, d: int, model: int = TDIST, s: int = 5,
+                 lr: float = 0.02, minibatch: int = 256, seed: int = 1,
+                 precision: int = FP32, flags: int = 0, stream=None):
+        self._lib = load_library()
+        self.n, self.d, self.s = int(n), int(d), int(s)
+        self.model, self.precision = int(model), int(precision)
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        if rp.size != self.n + 1:
+            raise ValueError(f"row_ptr has {rp.size} entries, expected n+1 = {self.n + 1}")
+        if ci.size == 0:
+            ci = np.zeros(1, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = self._lib.f2v_create_ex(_ptr(rp), _ptr(ci), self.n, self.d, int(model), self.s,
+                                     float(lr), int(minibatch), int(seed) & (2**64 - 1),
+                                     int(precision), int(flags), _stream_handle(stream),
+                                     ctypes.byref(h))
+        if rc != OK:
+            raise F2VError(rc, self._lib.f2v_last_error_global().decode())
+        self._h = h
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != OK:
+            msg = self._lib.f2v_last_error(self._h).decode() if self._h else ""
+            raise F2VError(rc, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.f2v_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- Algorithm 1 ------------------------------------------------------
+    def epoch(self):
+        self._check(self._lib.f2v_epoch(self._h))
+
+    def train(self, epochs: int):
+        self._check(self._lib.f2v_train(self._h, int(epochs)))
+
+    def run_minibatches(self, count: int):
+        self._check(self._lib.f2v_run_minibatches(self._h, int(count)))
+
+    @property
+    def progress(self) -> tuple[int, int]:
+        e = ctypes.c_int32()
+        k = ctypes.c_int32()
+        self._check(self._lib.f2v_get_progress(self._h, ctypes.byref(e), ctypes.byref(k)))
+        return e.value, k.value
+
+    def synchronize(self):
+        self._check(self._lib.f2v_synchronize(self._h))
+
+    def embedding(self) -> np.ndarray:
+        out = np.empty((self.n, self.d), dtype=np.float32)
+        self._check(self._lib.f2v_get_embedding(self._h, _ptr(out), out.size))
+        return out
+
+    def embedding_into_host(self, out: np.ndarray):
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.n * self.d
+        self._check(self._lib.f2v_get_embedding(self._h, _ptr(out), out.size))
+
+    def embedding_into_device(self, dev_ptr: int):
+        self._check(self._lib.f2v_get_embedding_device(self._h, ctypes.c_void_p(dev_ptr),
+                                                       self.n * self.d))
+
+    def set_embedding(self, z):
+        z = np.ascontiguousarray(z, dtype=np.float32)
+        self._check(self._lib.f2v_set_embedding(self._h, _ptr(z), z.size))
+
+    def set_lr(self, lr: float):
+        self._check(self._lib.f2v_set_lr(self._h, float(lr)))
+
+    def set_schedule(self, schedule: int, total_epochs: int):
+        self._check(self._lib.f2v_set_schedule(self._h, int(schedule), int(total_epochs)))
+
+    def set_epoch(self, epoch: int):
+        self._check(self._lib.f2v_set_epoch(self._h, int(epoch)))
+
+    @property
+    def epoch_counter(self) -> int:
+        e = ctypes.c_int32()
+        self._check(self._lib.f2v_get_epoch(self._h, ctypes.byref(e)))
+        return e.value
+
+    def set_stream(self, stream):
+        self._check(self._lib.f2v_set_stream(self._h, _stream_handle(stream)))
+
+    # -- evaluation and introspection -------------------------------------
+    def eval_auc(self, pos_pairs, neg_pairs) -> float:
+        pos = np.ascontiguousarray(pos_pairs, dtype=np.int32).reshape(-1, 2)
+        neg = np.ascontiguousarray(neg_pairs, dtype=np.int32).reshape(-1, 2)
+        out = ctypes.c_double()
+        self._check(self._lib.f2v_eval_auc(self._h, _ptr(pos), pos.shape[0], _ptr(neg),
+                                           neg.shape[0], ctypes.byref(out)))
+        return out.value
+
+    def debug_samples(self, epoch: int) -> np.ndarray:
+        out = np.zeros((self.n, self.s), dtype=np.int32)
+        buf = out if out.size else np.zeros(1, np.int32)
+        self._check(self._lib.f2v_debug_samples(self._h, int(epoch), _ptr(buf), out.size))
+        return out
+
+    @property
+    def pairs_per_epoch(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.f2v_pairs_per_epoch(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        self._check(self._lib.f2v_device_bytes(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.f2v_launch_count(self._h, ctypes.byref(v)))
+        return v.value
+
+    def set_kernel_timing(self, enable: bool):
+        self._check(self._lib.f2v_set_kernel_timing(self._h, 1 if enable else 0))
+
+    def read_kernel_timing(self) -> tuple[int, float]:
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        self._check(self._lib.f2v_read_kernel_timing(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+
+def create(graph, d: int, **kw) -> Context:
+    """Context for a ``graphs.Graph``."""
+    return Context(graph.row_ptr, graph.col_idx, graph.n, d, **kw)

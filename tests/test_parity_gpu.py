@@ -1,0 +1,368 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: after one epoch every element of Z must satisfy
+|z_gpu - z_oracle| / max(|z_oracle|, 1e-3) <= 1e-5 (FP32 path).  Integer work
+(negative-sample indices, the initial embedding, which is exact in FP32) must
+match bit for bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2009_10035_gb300 import f2v, graphs
+
+pytestmark = pytest.mark.gpu
+
+TOL_1EPOCH = 1e-5
+TOL_STEP = 1e-5
+FLOOR = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    f2v.load_library()
+
+
+def rel_err(got, want):
+    return np.abs(np.asarray(got, np.float64) - want) / np.maximum(np.abs(want), FLOOR)
+
+
+def gpu_run(g, d, model, s, b, lr, seed, epochs, precision=f2v.FP32, schedule=None,
+            total_epochs=0, z0=None):
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                     seed=seed, precision=precision) as ctx:
+        if schedule is not None:
+            ctx.set_schedule(schedule, total_epochs)
+        if z0 is not None:
+            ctx.set_embedding(z0)
+        ctx.train(epochs)
+        return ctx.embedding()
+
+
+def oracle_run(g, d, model, s, b, lr, seed, epochs, schedule=0, total_epochs=0, z0=None):
+    Z0 = oracle.init_embedding(g.n, d, seed) if z0 is None else np.asarray(z0, np.float64)
+    return oracle.train(model, g.row_ptr, g.col_idx, Z0, s, b, seed, lr, epochs,
+                        schedule=schedule, total_epochs=total_epochs)
+
+
+def check_parity(g, d, model, s, b, lr=0.02, seed=1, epochs=1, tol=TOL_1EPOCH, **kw):
+    """Whole run against the oracle, element by element (well-conditioned cases)."""
+    got = gpu_run(g, d, model, s, b, lr, seed, epochs, **kw)
+    want = oracle_run(g, d, model, s, b, lr, seed, epochs)
+    assert np.isfinite(got).all()
+    err = rel_err(got, want)
+    assert err.max() <= tol, f"max rel err {err.max():.3e} at {np.unravel_index(err.argmax(), err.shape)}"
+    return err.max()
+
+
+def bf16_round(x):
+    """FP32 -> BF16 (round to nearest even) -> FP64, for finite x."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedule=None,
+                total_epochs=0, precision=f2v.FP32, tol=TOL_STEP):
+    """Minibatch by minibatch: the oracle computes each checked minibatch's
+    update (Algorithm 2 + Eq. 10) from the GPU's own Z before it, so that each
+    kernel launch is compared in isolation.  Error bound: FP32 accumulation of
+    z_u - eta * sum(terms) is accurate relative to |z_u| + eta * sum|terms|,
+    so the error is measured against that scale (floor 1e-3)."""
+    M = -(-g.n // b)
+    worst = 0.0
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                     seed=seed, precision=precision) as ctx:
+        if schedule is not None:
+            ctx.set_schedule(schedule, total_epochs)
+        for e in range(epochs):
+            for k in range(M):
+                if steps is not None and (e, k) not in steps:
+                    ctx.run_minibatches(1)
+                    continue
+                assert ctx.progress == (e, k)
+                before = ctx.embedding().astype(np.float64)
+                ctx.run_minibatches(1)
+                after = ctx.embedding().astype(np.float64)
+                u0, u1 = k * b, min(g.n, (k + 1) * b)
+                gather = bf16_round(before) if precision == f2v.BF16 else None
+                G, A = oracle.grad_minibatch_abs(model, g.row_ptr, g.col_idx, before, u0, u1,
+                                                 s, seed, e, gather=gather)
+                eta = oracle.learning_rate(lr, 0 if schedule is None else schedule,
+                                           total_epochs, e)
+                want = before[u0:u1] - eta * G
+                scale = np.maximum(np.abs(before[u0:u1]) + eta * A, FLOOR)
+                err = np.abs(after[u0:u1] - want) / scale
+                assert np.isfinite(after).all()
+                assert err.max() <= tol, (f"epoch {e} minibatch {k}: scaled err {err.max():.3e} "
+                                          f"at row {u0 + np.unravel_index(err.argmax(), err.shape)[0]}")
+                assert np.array_equal(after[:u0], before[:u0])
+                assert np.array_equal(after[u1:], before[u1:])
+                worst = max(worst, float(err.max()))
+    return worst
+
+
+MODELS = [pytest.param(f2v.TDIST, id="tdist"), pytest.param(f2v.SIGMOID, id="sigmoid")]
+
+
+# ---------------------------------------------------------------- integer work
+
+@pytest.mark.parametrize("d", [2, 32, 100, 128])
+def test_initial_embedding_bit_exact(d):
+    g = graphs.erdos_renyi(500, p=0.01, seed=2)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, seed=0xABCDEF0123) as ctx:
+        got = ctx.embedding()
+    want = oracle.init_embedding(g.n, d, 0xABCDEF0123)
+    assert np.array_equal(got.astype(np.float64), want)
+
+
+def test_initial_embedding_bit_exact_bf16_master():
+    g = graphs.erdos_renyi(300, p=0.02, seed=2)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 64, seed=5, precision=f2v.BF16) as ctx:
+        got = ctx.embedding()
+    assert np.array_equal(got.astype(np.float64), oracle.init_embedding(g.n, 64, 5))
+
+
+@pytest.mark.parametrize("n,s", [(1000, 5), (1, 3), (7919, 10), (1 << 20, 5)])
+def test_negative_samples_bit_exact(n, s):
+    g = graphs.from_edges(n, [], [])
+    seed = 0x1234_5678_9ABC
+    with f2v.Context(g.row_ptr, g.col_idx, n, 8, s=s, seed=seed) as ctx:
+        for e in (0, 1, 19):
+            assert np.array_equal(ctx.debug_samples(e), oracle.samples(n, s, e, seed))
+
+
+# ---------------------------------------------------------------- one epoch
+
+@pytest.mark.parametrize("model", MODELS)
+def test_er_n1000_d32_one_epoch(model):
+    """Erdos-Renyi n=1000, ~10,000 edges, d=32, s=5, b=256, lr=0.02."""
+    g = graphs.config1_graph()
+    check_parity(g, 32, model, s=5, b=256, lr=0.02, seed=1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 8, 16, 24, 64, 100, 128, 256, 512, 1024])
+def test_dimensions(model, d):
+    g = graphs.erdos_renyi(400, p=0.03, seed=d)
+    check_steps(g, d, model, s=5, b=128, lr=0.02, seed=d + 1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [4, 16, 32, 64, 128, 256])
+def test_dimensions_whole_epoch(model, d):
+    """Well-conditioned sizes also meet the element-wise bound over an epoch."""
+    g = graphs.erdos_renyi(400, p=0.03, seed=d)
+    check_parity(g, d, model, s=5, b=128, lr=0.02, seed=d + 1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("b", [1, 3, 250, 299, 300, 1000])
+def test_minibatch_sizes(model, b):
+    g = graphs.erdos_renyi(300, p=0.04, seed=4)
+    check_steps(g, 32, model, s=3, b=b, lr=0.05, seed=9)
+    check_parity(g, 32, model, s=3, b=b, lr=0.05, seed=9)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [16, 128])
+def test_hub_spanning_many_items(model, d):
+    """A star of 5000 leaves plus a sparse random graph: the hub's pairs span
+    ~160 items, summed through the partial-slot protocol."""
+    star = graphs.star(5000)
+    er = graphs.erdos_renyi(star.n, m=8000, seed=3)
+    src = np.concatenate([np.repeat(np.arange(star.n), star.degrees()),
+                          np.repeat(np.arange(er.n), er.degrees())])
+    dst = np.concatenate([star.col_idx, er.col_idx])
+    g = graphs.from_edges(star.n, src, dst)
+    check_steps(g, d, model, s=5, b=700, lr=0.01, seed=3)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_skewed_rmat(model):
+    g = graphs.rmat(13, 16, seed=5)
+    check_steps(g, 64, model, s=5, b=1024, lr=0.02, seed=5)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_isolated_vertices_without_samples_keep_their_rows(model):
+    g = graphs.erdos_renyi(200, p=0.01, seed=8)       # has isolated vertices
+    iso = np.nonzero(g.degrees() == 0)[0]
+    assert iso.size > 0
+    got = gpu_run(g, 16, model, 0, 64, 0.1, 4, 2)
+    Z0 = oracle.init_embedding(g.n, 16, 4)
+    assert np.array_equal(got[iso].astype(np.float64), Z0[iso])
+    want = oracle_run(g, 16, model, 0, 64, 0.1, 4, 2)
+    assert rel_err(got, want).max() <= 2 * TOL_1EPOCH
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_tiny_graphs(model, n):
+    g = graphs.from_edges(n, list(range(n - 1)), list(range(1, n)))   # a path
+    check_steps(g, 8, model, s=4, b=2, lr=0.1, seed=2, epochs=2)
+    check_parity(g, 8, model, s=4, b=2, lr=0.1, seed=2)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_edgeless_graph(model):
+    g = graphs.from_edges(64, [], [])
+    check_steps(g, 32, model, s=5, b=16, lr=0.05, seed=3)
+    check_parity(g, 32, model, s=5, b=16, lr=0.05, seed=3)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_steps_across_epochs_with_linear_schedule(model):
+    g = graphs.erdos_renyi(700, m=6000, seed=12)
+    check_steps(g, 16, model, s=5, b=200, lr=0.05, seed=4, epochs=3,
+                schedule=f2v.LR_LINEAR, total_epochs=3)
+
+
+def test_split_epoch_equals_whole_epoch():
+    """Running an epoch in pieces (with reads of Z in between) gives the same
+    bits as running it at once."""
+    g = graphs.rmat(11, 8, seed=9)
+    whole = gpu_run(g, 64, f2v.SIGMOID, 5, 300, 0.02, 2, 2)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 64, model=f2v.SIGMOID, s=5, lr=0.02,
+                     minibatch=300, seed=2) as ctx:
+        ctx.run_minibatches(3)
+        ctx.embedding()
+        ctx.epoch()                     # finishes epoch 0
+        assert ctx.progress == (1, 0)
+        ctx.run_minibatches(5)
+        assert ctx.progress == (1, 5)
+        ctx.run_minibatches(2)          # 2048 / 300 -> 7 minibatches: crosses into epoch 2
+        assert ctx.progress == (2, 0)
+        assert np.array_equal(ctx.embedding(), whole)
+
+
+# ---------------------------------------------------------------- several epochs
+
+@pytest.mark.parametrize("model", MODELS)
+def test_three_epochs_linear_schedule(model):
+    g = graphs.config1_graph()
+    got = gpu_run(g, 32, model, 5, 256, 0.02, 1, 3, schedule=f2v.LR_LINEAR, total_epochs=3)
+    want = oracle_run(g, 32, model, 5, 256, 0.02, 1, 3, schedule=1, total_epochs=3)
+    assert rel_err(got, want).max() <= 1e-4
+
+
+def test_runs_are_bit_reproducible():
+    g = graphs.rmat(12, 8, seed=2)
+    a = gpu_run(g, 128, f2v.TDIST, 5, 512, 0.02, 3, 2)
+    b = gpu_run(g, 128, f2v.TDIST, 5, 512, 0.02, 3, 2)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_resume_is_bit_identical(model):
+    g = graphs.config1_graph()
+    full = gpu_run(g, 32, model, 5, 256, 0.02, 7, 3)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, lr=0.02,
+                     minibatch=256, seed=7) as ctx:
+        ctx.train(2)
+        mid = ctx.embedding()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, lr=0.02,
+                     minibatch=256, seed=7) as ctx:
+        ctx.set_embedding(mid)
+        ctx.set_epoch(2)
+        ctx.epoch()
+        assert ctx.epoch_counter == 3
+        resumed = ctx.embedding()
+    assert np.array_equal(full, resumed)
+
+
+# ---------------------------------------------------------------- evaluation
+
+@pytest.mark.parametrize("model", MODELS)
+def test_auc_matches_oracle_on_same_embedding(model):
+    g = graphs.holdout(graphs.erdos_renyi(2000, m=20000, seed=4), 0.1, seed=5)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, minibatch=256,
+                     seed=2) as ctx:
+        ctx.train(5)
+        Z = ctx.embedding().astype(np.float64)
+        got = ctx.eval_auc(g.test_pos, g.test_neg)
+    want = oracle.link_auc(model, Z, g.test_pos, g.test_neg)
+    assert abs(got - want) < 1e-9
+
+
+def test_error_status_for_bad_arguments():
+    g = graphs.config1_graph()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32) as ctx:
+        with pytest.raises(f2v.F2VError):
+            ctx.set_embedding(np.zeros(5, np.float32))
+        with pytest.raises(f2v.F2VError):
+            ctx.eval_auc(np.array([[0, 5000]]), np.array([[0, 1]]))
+        ctx.epoch()                                       # still usable
+        ctx.synchronize()
+
+
+# ---------------------------------------------------------------- BF16 storage form
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [2, 16, 64, 128, 100])
+def test_bf16_storage_steps(model, d):
+    """BF16 partner rows, FP32 master own rows, FP32 accumulation: each launch
+    matches the oracle fed the same BF16-rounded partner rows."""
+    g = graphs.rmat(12, 8, seed=d)
+    check_steps(g, d, model, s=5, b=512, lr=0.02, seed=3, epochs=2, precision=f2v.BF16)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_bf16_bit_reproducible_and_resumable(model):
+    g = graphs.rmat(11, 8, seed=4)
+    a = gpu_run(g, 128, model, 5, 256, 0.02, 3, 3, precision=f2v.BF16)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, model=model, s=5, lr=0.02,
+                     minibatch=256, seed=3, precision=f2v.BF16) as ctx:
+        ctx.train(2)
+        mid = ctx.embedding()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, model=model, s=5, lr=0.02,
+                     minibatch=256, seed=3, precision=f2v.BF16) as ctx:
+        ctx.set_embedding(mid)
+        ctx.set_epoch(2)
+        ctx.epoch()
+        b = ctx.embedding()
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------- full size
+
+@pytest.fixture(scope="module")
+def rmat20():
+    return graphs.config2_graph()
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_rmat_scale20_d128_one_epoch(model, rmat20):
+    """R-MAT scale 20 (2^20 vertices, ~30M CSR entries after the 5% hold-out),
+    d=128, s=5, b=4096: the benchmark's workload and launch configuration.
+    Sampled minibatches are checked one launch at a time: the first, the one
+    holding the largest hub (~61k neighbours), a middle one and the last."""
+    g = rmat20
+    b = 4096
+    M = -(-g.n // b)
+    hub_mb = int(np.argmax(g.degrees())) // b
+    steps = {(0, 0), (0, hub_mb), (0, M // 2 + 1), (0, M - 1)}
+    worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps,
+                        schedule=f2v.LR_LINEAR, total_epochs=20)
+    print(f"rmat20 model={model}: worst scaled error {worst:.3e}")
+
+
+@pytest.mark.skipif(os.environ.get("F2V_FULL") != "1", reason="set F2V_FULL=1 (minutes of CPU)")
+@pytest.mark.parametrize("model", MODELS)
+def test_rmat_scale20_auc_after_20_epochs(model, rmat20):
+    g = rmat20
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, model=model, s=5, lr=0.02,
+                     minibatch=4096, seed=1) as ctx:
+        ctx.set_schedule(f2v.LR_LINEAR, 20)
+        ctx.train(20)
+        auc_gpu = ctx.eval_auc(g.test_pos, g.test_neg)
+    Zo = oracle_run(g, 128, model, 5, 4096, 0.02, 1, 20, schedule=1, total_epochs=20)
+    auc_oracle = oracle.link_auc(model, Zo, g.test_pos, g.test_neg)
+    print(f"AUC model={model}: gpu {auc_gpu:.5f} oracle {auc_oracle:.5f}")
+    assert abs(auc_gpu - auc_oracle) <= 0.005
