@@ -73,6 +73,8 @@ typedef enum { F2V_LR_CONSTANT = 0, F2V_LR_LINEAR = 1 } f2v_schedule;
 
 /* f2v_create_ex flags */
 #define F2V_FLAG_CHECK_SYMMETRY 0x1u   /* reject a CSR that is not symmetric */
+#define F2V_FLAG_NO_STAGING 0x2u       /* use the register-gather kernel even where
+                                          the shared-memory staged one exists */
 
 /*
  * Creates a context for one graph on the current CUDA device: validates and

@@ -122,14 +122,18 @@ struct f2v_ctx {
     int epoch = 0;
     cudaStream_t stream = nullptr;
     Shape shape{};
-    int C = 32;
+    int C = 32;                            // pairs per item (register kernel)
+    bool bulk = false;                     // shared-memory staged kernel in use
+    int bulk_warps = 0, bulk_smem = 0, bulk_sms = 0;
 
     // host copies of the schedule of work
     std::vector<int64_t> h_apair;          // n + 1
     std::vector<int64_t> mb_item_base;     // M + 1
+    std::vector<int32_t> mb_C;             // pairs per item (chunk) of each minibatch
     int64_t max_items = 0;
 
     // device buffers
+    int32_t *err_word = nullptr;           // set by a device wait that timed out
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *item_u0 = nullptr, *counter = nullptr;
     int64_t *apair = nullptr;
     void *z[2] = {nullptr, nullptr};       // float or bf16 rows
@@ -206,7 +210,7 @@ void release(f2v_ctx *c)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    void *bufs[] = {c->row_ptr, c->col_idx, c->item_u0, c->counter, c->apair,
+    void *bufs[] = {c->err_word, c->row_ptr, c->col_idx, c->item_u0, c->counter, c->apair,
                     c->z[0], c->z[1], c->master};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -278,16 +282,24 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
     }
     const int M = (n + c->b - 1) / c->b;
     c->mb_item_base.assign((size_t)M + 1, 0);
+    c->mb_C.assign((size_t)M, c->C);
     items.clear();
     c->max_items = 0;
+    const int64_t W = (int64_t)c->bulk_sms * c->bulk_warps;   // warps of a staged launch
     for (int k = 0; k < M; ++k) {
         const int u0 = k * c->b, u1 = std::min(n, u0 + c->b);
         const int64_t P0 = c->h_apair[(size_t)u0], P1 = c->h_apair[(size_t)u1];
-        if (P1 - P0 >= (int64_t)INT32_MAX - c->C) return false;
-        const int64_t nit = (P1 - P0 + c->C - 1) / c->C;
+        int64_t C = c->C;
+        if (c->bulk) {   // one chunk per warp, a multiple of 32 pairs
+            C = (P1 - P0 + W - 1) / W;
+            C = std::max<int64_t>(32, (C + 31) / 32 * 32);
+        }
+        if (P1 - P0 >= (int64_t)INT32_MAX - C) return false;
+        c->mb_C[(size_t)k] = (int32_t)C;
+        const int64_t nit = (P1 - P0 + C - 1) / C;
         int u = u0;
         for (int64_t i = 0; i < nit; ++i) {
-            const int64_t q = P0 + i * c->C;
+            const int64_t q = P0 + i * C;
             while (c->h_apair[(size_t)u + 1] <= q) ++u;
             items.push_back(u);
         }
@@ -347,6 +359,53 @@ f2v_status get_event(f2v_ctx *c, cudaEvent_t *e)
 
 int num_minibatches(const f2v_ctx *c) { return (c->n + c->b - 1) / c->b; }
 
+// Reads (and clears) the device error word after the stream has drained.
+// A set word means a bounded device wait ran out: the epoch's result is not
+// valid, and the context is marked failed.
+f2v_status check_device_error(f2v_ctx *c)
+{
+    int32_t word = 0;
+    F2V_CUDA(c, cudaMemcpyAsync(&word, c->err_word, sizeof word, cudaMemcpyDeviceToHost,
+                                c->stream));
+    F2V_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (word != 0) {
+        c->failed = true;
+        c->err = "a device-side wait timed out; results of the last epochs are not valid";
+        return F2V_ETIMEOUT;
+    }
+    return F2V_OK;
+}
+
+// Arguments of the force kernel for minibatch k of the current epoch.
+template <typename Ts>
+void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
+{
+    const int u0 = k * c->b, u1 = std::min(c->n, u0 + c->b);
+    a.row_ptr = c->row_ptr;
+    a.col_idx = c->col_idx;
+    a.apair = c->apair;
+    a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
+    a.zcur = (const Ts *)c->z[c->cur];
+    a.znext = (Ts *)c->z[c->cur ^ 1];
+    a.counter = c->counter;
+    a.slots = c->slots;
+    a.unit_cnt = c->unit_cnt;
+    a.units0 = std::max<int64_t>(c->max_items, 1);
+    a.P0 = c->h_apair[(size_t)u0];
+    a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
+    a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
+    a.mb_begin = u0;
+    a.mb_end = u1;
+    a.n = c->n; a.d = c->d; a.ld = c->ld; a.s = c->s;
+    a.C = c->mb_C[(size_t)k];
+    a.epoch = (uint32_t)c->epoch;
+    a.key0 = (uint32_t)c->seed;
+    a.key1 = (uint32_t)(c->seed >> 32);
+    a.eta = eta;
+    a.model = c->model;
+    a.err = c->err_word;
+}
+
 // Launches the force kernel of minibatch k of the current epoch.
 f2v_status run_minibatch(f2v_ctx *c, int k)
 {
@@ -364,34 +423,22 @@ f2v_status run_minibatch(f2v_ctx *c, int k)
     cudaError_t err;
     if (c->precision == F2V_BF16) {
         ForceArgs<__nv_bfloat16> a{};
-        a.row_ptr = c->row_ptr; a.col_idx = c->col_idx; a.apair = c->apair;
-        a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
-        a.zcur = (const __nv_bfloat16 *)c->z[c->cur];
-        a.znext = (__nv_bfloat16 *)c->z[nxt];
-        a.master = c->master; a.counter = c->counter;
-        a.slots = c->slots; a.unit_cnt = c->unit_cnt; a.units0 = std::max<int64_t>(c->max_items, 1);
-        a.P0 = c->h_apair[(size_t)u0]; a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
-        a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
-        a.mb_begin = u0; a.mb_end = u1;
-        a.n = c->n; a.d = c->d; a.ld = c->ld; a.s = c->s; a.C = c->C;
-        a.epoch = (uint32_t)e; a.key0 = (uint32_t)c->seed; a.key1 = (uint32_t)(c->seed >> 32);
-        a.eta = eta; a.model = c->model;
-        err = launch_force_bf16(c->shape, a, c->blocks_cap, c->stream);
+        fill_args(c, k, eta, a);
+        a.master = c->master;
+        if (c->bulk)
+            err = launch_bulk_bf16(c->d, a, (a.n_items + c->bulk_warps - 1) / c->bulk_warps,
+                                   c->bulk_warps, c->bulk_smem, c->stream);
+        else
+            err = launch_force_bf16(c->shape, a, c->blocks_cap, c->stream);
     } else {
         ForceArgs<float> a{};
-        a.row_ptr = c->row_ptr; a.col_idx = c->col_idx; a.apair = c->apair;
-        a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
-        a.zcur = (const float *)c->z[c->cur];
-        a.znext = (float *)c->z[nxt];
-        a.master = nullptr; a.counter = c->counter;
-        a.slots = c->slots; a.unit_cnt = c->unit_cnt; a.units0 = std::max<int64_t>(c->max_items, 1);
-        a.P0 = c->h_apair[(size_t)u0]; a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
-        a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
-        a.mb_begin = u0; a.mb_end = u1;
-        a.n = c->n; a.d = c->d; a.ld = c->ld; a.s = c->s; a.C = c->C;
-        a.epoch = (uint32_t)e; a.key0 = (uint32_t)c->seed; a.key1 = (uint32_t)(c->seed >> 32);
-        a.eta = eta; a.model = c->model;
-        err = launch_force_fp32(c->shape, a, c->blocks_cap, c->stream);
+        fill_args(c, k, eta, a);
+        a.master = nullptr;
+        if (c->bulk)
+            err = launch_bulk_fp32(c->d, a, (a.n_items + c->bulk_warps - 1) / c->bulk_warps,
+                                   c->bulk_warps, c->bulk_smem, c->stream);
+        else
+            err = launch_force_fp32(c->shape, a, c->blocks_cap, c->stream);
     }
     c->launches++;
     if (err != cudaSuccess)
@@ -498,6 +545,16 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
     c->shape = choose_shape(d);
     c->C = items_pairs(c->shape);
 
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    sms = std::max(sms, 1);
+    c->blocks_cap = sms * 8;
+    if (!(flags & F2V_FLAG_NO_STAGING) &&
+        bulk_config(d, precision == F2V_BF16, &c->bulk_warps, &c->bulk_smem)) {
+        c->bulk = true;
+        c->bulk_sms = sms;
+    }
+
     std::vector<int32_t> items;
     try {
         if (!build_schedule(c, row_ptr, items)) {
@@ -510,14 +567,11 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         return fail(nullptr, F2V_ENOMEM, "host allocation failed (schedule)");
     }
 
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    per_sm = 8;
-    c->blocks_cap = std::max(1, sms * per_sm);
 
     const size_t es = elem_size(c);
     const size_t zbytes = (size_t)n * (size_t)c->ld * es;
     st = F2V_OK;
+    if (st == F2V_OK) st = alloc(c, (void **)&c->err_word, sizeof(int32_t));
     if (st == F2V_OK) st = alloc(c, (void **)&c->row_ptr, sizeof(int32_t) * ((size_t)n + 1));
     if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx, sizeof(int32_t) * (size_t)c->nnz);
     if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
@@ -573,6 +627,7 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         CREATE_CUDA(cudaMemcpyAsync(c->item_u0, items.data(), sizeof(int32_t) * items.size(),
                                     cudaMemcpyHostToDevice, c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(int32_t) * (size_t)n, c->stream));
+    CREATE_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(int32_t), c->stream));
     CREATE_CUDA(launch_init(c));
     CREATE_CUDA(cudaStreamSynchronize(c->stream));
 #undef CREATE_CUDA
@@ -634,7 +689,7 @@ f2v_status f2v_synchronize(f2v_ctx *ctx)
     DeviceGuard g(ctx->device);
     F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     F2V_CUDA(ctx, cudaGetLastError());
-    return F2V_OK;
+    return check_device_error(ctx);
 }
 
 f2v_status f2v_get_embedding(f2v_ctx *ctx, float *out, size_t count)

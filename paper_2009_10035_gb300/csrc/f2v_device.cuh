@@ -121,4 +121,36 @@ __device__ __forceinline__ void store_vec(__nv_bfloat16 *p, const float *x)
     }
 }
 
+// Shared-memory vector loads, widened to FP32.
+template <int VEC>
+__device__ __forceinline__ void load_vec_smem(const float *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else if constexpr (VEC == 2) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        x[0] = t.x; x[1] = t.y;
+    } else {
+        x[0] = p[0];
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_vec_smem(const __nv_bfloat16 *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    } else if constexpr (VEC == 2) {
+        const unsigned int t = *reinterpret_cast<const unsigned int *>(p);
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
+        x[0] = a.x; x[1] = a.y;
+    } else {
+        x[0] = __bfloat162float(p[0]);
+    }
+}
+
 }  // namespace f2v

@@ -131,6 +131,73 @@ __device__ __forceinline__ int64_t unit_slot(int64_t j, int lb, int64_t unit_pai
     return ((int64_t)lb <= j * unit_pairs) ? 2 * j : 2 * j + 1;
 }
 
+// Finishes vertex u, whose local pairs are [vbeg, vend) and whose pairs in
+// level-0 unit `unit0` are summed in g: writes z_u - eta * g if the unit held
+// all of them, else passes the part up the ordered combine tree (g is
+// clobbered).
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, unsigned gmask, int gl,
+                                              int unit0, int u, int vbeg, int vend,
+                                              const float *zu, float *g)
+{
+    constexpr int E = VEC * NV;
+    int64_t fu = vbeg / a.C, lu = (vend - 1) / a.C;
+    if (fu == lu) {
+        write_row<L, VEC, NV, EXACT>(a, u, gl, zu, g);
+        return;
+    }
+    int64_t unit = unit0, unit_pairs = a.C, units = a.units0;
+    float *slot_base = a.slots;
+    int32_t *cnt_base = a.unit_cnt;
+    for (int lvl = 0; lvl + 1 < kMaxLevels; ++lvl) {
+        store_row_cg<L, VEC, NV, EXACT>(slot_base + unit_slot(unit, vbeg, unit_pairs) * a.ld,
+                                        gl, a.d, g);
+        __threadfence();
+        __syncwarp(gmask);
+        const int64_t parent = unit / kFan;
+        const int64_t pfu = fu / kFan, plu = lu / kFan;
+        const int64_t c0 = max(fu, parent * kFan);
+        const int64_t c1 = min(lu, parent * kFan + (kFan - 1));
+        const bool top = (pfu == plu);
+        const int64_t punits = (units + kFan - 1) / kFan;
+        int32_t *cnt = top ? &a.counter[u]
+                           : &cnt_base[unit_slot(parent, vbeg, unit_pairs * kFan)];
+        int prior = 0;
+        if (gl == 0) prior = atomicAdd(cnt, 1);
+        prior = __shfl_sync(gmask, prior, 0, L);
+        if (prior != (int)(c1 - c0)) return;      // a sibling completes it
+        __threadfence();
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = 0.f;
+        for (int64_t c = c0; c <= c1; c += 4) {    // children in order
+            float part[4][E];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k <= c1)
+                    load_row_cg<L, VEC, NV, EXACT>(
+                        slot_base + unit_slot(c + k, vbeg, unit_pairs) * a.ld, gl, a.d, part[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k <= c1) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) g[e] += part[k][e];
+                }
+        }
+        if (gl == 0) *cnt = 0;
+        if (top) {
+            write_row<L, VEC, NV, EXACT>(a, u, gl, zu, g);
+            return;
+        }
+        slot_base += 2 * units * a.ld;
+        cnt_base += 2 * punits;
+        unit = parent;
+        fu = pfu;
+        lu = plu;
+        units = punits;
+        unit_pairs *= kFan;
+    }
+}
+
 template <int L, int VEC, int NV, bool EXACT, typename Ts>
 __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
 {
@@ -220,63 +287,7 @@ __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
             const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
             if (w != ucur) {
                 // ---- 4. update: the only place a vertex is finished ------
-                int64_t fu = vbeg / a.C, lu = (vend - 1) / a.C;
-                if (fu == lu) {
-                    write_row<L, VEC, NV, EXACT>(a, ucur, gl, zu, g);
-                } else {
-                    // pass the part up the ordered combine tree
-                    int64_t unit = item, unit_pairs = a.C, units = a.units0;
-                    float *slot_base = a.slots;
-                    int32_t *cnt_base = a.unit_cnt;
-                    for (int lvl = 0; lvl + 1 < kMaxLevels; ++lvl) {
-                        store_row_cg<L, VEC, NV, EXACT>(
-                            slot_base + unit_slot(unit, vbeg, unit_pairs) * a.ld, gl, a.d, g);
-                        __threadfence();
-                        __syncwarp(gmask);
-                        const int64_t parent = unit / kFan;
-                        const int64_t pfu = fu / kFan, plu = lu / kFan;
-                        const int64_t c0 = max(fu, parent * kFan);
-                        const int64_t c1 = min(lu, parent * kFan + (kFan - 1));
-                        const bool top = (pfu == plu);
-                        const int64_t punits = (units + kFan - 1) / kFan;
-                        int32_t *cnt = top ? &a.counter[ucur]
-                                           : &cnt_base[unit_slot(parent, vbeg, unit_pairs * kFan)];
-                        int prior = 0;
-                        if (gl == 0) prior = atomicAdd(cnt, 1);
-                        prior = __shfl_sync(gmask, prior, 0, L);
-                        if (prior != (int)(c1 - c0)) break;   // a sibling completes it
-                        __threadfence();
-#pragma unroll
-                        for (int e = 0; e < E; ++e) g[e] = 0.f;
-                        for (int64_t c = c0; c <= c1; c += 4) {    // children in order
-                            float part[4][E];
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (c + k <= c1)
-                                    load_row_cg<L, VEC, NV, EXACT>(
-                                        slot_base + unit_slot(c + k, vbeg, unit_pairs) * a.ld, gl,
-                                        a.d, part[k]);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (c + k <= c1) {
-#pragma unroll
-                                    for (int e = 0; e < E; ++e) g[e] += part[k][e];
-                                }
-                        }
-                        if (gl == 0) *cnt = 0;
-                        if (top) {
-                            write_row<L, VEC, NV, EXACT>(a, ucur, gl, zu, g);
-                            break;
-                        }
-                        slot_base += 2 * units * a.ld;
-                        cnt_base += 2 * punits;
-                        unit = parent;
-                        fu = pfu;
-                        lu = plu;
-                        units = punits;
-                        unit_pairs *= kFan;
-                    }
-                }
+                finish_vertex<L, VEC, NV, EXACT>(a, gmask, gl, item, ucur, vbeg, vend, zu, g);
                 if (w < 0) break;
                 // next vertex: always ucur + 1, its own row already fetched
                 ucur = w;

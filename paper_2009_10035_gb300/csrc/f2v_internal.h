@@ -62,6 +62,7 @@ struct ForceArgs {
     uint32_t key0, key1;       // Philox key = (seed lo, seed hi)
     float eta;
     int32_t model;             // 0 = t-distribution, 1 = sigmoid
+    int32_t *err;              // device error word (1 = a bounded wait timed out)
 };
 
 // Kernel shape chosen from d: a group of L lanes owns one force pair at a
@@ -75,6 +76,15 @@ Shape choose_shape(int d);
 
 // Pairs per item for a shape.
 int items_pairs(const Shape &sh);
+
+// The shared-memory staged kernel (f2v_bulk.cuh) serves FP32 and BF16 rows
+// of d in {64, 128, 256}; it runs `warps` warps per block, one block per SM,
+// each warp walking one chunk.  Returns false if d has no such kernel.
+bool bulk_config(int d, bool bf16, int *warps_per_block, int *smem_bytes);
+cudaError_t launch_bulk_fp32(int d, const ForceArgs<float> &a, int blocks, int warps,
+                             int smem_bytes, cudaStream_t st);
+cudaError_t launch_bulk_bf16(int d, const ForceArgs<__nv_bfloat16> &a, int blocks, int warps,
+                             int smem_bytes, cudaStream_t st);
 
 // Launches the force kernel for one minibatch.  Returns the CUDA error of the
 // launch.  `blocks_cap` bounds the grid (0 = no bound).

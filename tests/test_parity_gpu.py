@@ -34,9 +34,9 @@ def rel_err(got, want):
 
 
 def gpu_run(g, d, model, s, b, lr, seed, epochs, precision=f2v.FP32, schedule=None,
-            total_epochs=0, z0=None):
+            total_epochs=0, z0=None, flags=0):
     with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
-                     seed=seed, precision=precision) as ctx:
+                     seed=seed, precision=precision, flags=flags) as ctx:
         if schedule is not None:
             ctx.set_schedule(schedule, total_epochs)
         if z0 is not None:
@@ -69,7 +69,7 @@ def bf16_round(x):
 
 
 def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedule=None,
-                total_epochs=0, precision=f2v.FP32, tol=TOL_STEP):
+                total_epochs=0, precision=f2v.FP32, tol=TOL_STEP, flags=0):
     """Minibatch by minibatch: the oracle computes each checked minibatch's
     update (Algorithm 2 + Eq. 10) from the GPU's own Z before it, so that each
     kernel launch is compared in isolation.  Error bound: FP32 accumulation of
@@ -78,7 +78,7 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
     M = -(-g.n // b)
     worst = 0.0
     with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
-                     seed=seed, precision=precision) as ctx:
+                     seed=seed, precision=precision, flags=flags) as ctx:
         if schedule is not None:
             ctx.set_schedule(schedule, total_epochs)
         for e in range(epochs):
@@ -152,6 +152,17 @@ def test_er_n1000_d32_one_epoch(model):
 def test_dimensions(model, d):
     g = graphs.erdos_renyi(400, p=0.03, seed=d)
     check_steps(g, d, model, s=5, b=128, lr=0.02, seed=d + 1)
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [64, 128, 256])
+@pytest.mark.parametrize("precision", [f2v.FP32, f2v.BF16], ids=["fp32", "bf16"])
+def test_register_kernel_where_staged_exists(model, d, precision):
+    """The register-gather kernel (F2V_FLAG_NO_STAGING) is kept exact for the
+    sizes where the shared-memory staged kernel is the default."""
+    g = graphs.rmat(11, 8, seed=d)
+    check_steps(g, d, model, s=5, b=300, lr=0.02, seed=d, precision=precision,
+                flags=f2v.FLAG_NO_STAGING)
 
 
 @pytest.mark.parametrize("model", MODELS)
