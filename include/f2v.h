@@ -179,6 +179,48 @@ f2v_status f2v_launch_count(const f2v_ctx *ctx, int64_t *launches);
 f2v_status f2v_set_kernel_timing(f2v_ctx *ctx, int32_t enable);
 f2v_status f2v_read_kernel_timing(f2v_ctx *ctx, int64_t *launches, double *total_ms);
 
+/*
+ * One minibatch of an epoch on caller-owned device buffers, allocating
+ * nothing.  (The paper has no counterpart: this exists for callers that
+ * cannot allocate device memory while the step runs -- software that owns
+ * all device memory through its own allocator or arena and forbids libraries
+ * from calling cudaMalloc, or that plans its memory for the whole run up
+ * front -- and therefore cannot use f2v_create, which allocates.)
+ *
+ * All pointers are device memory owned by the caller: the CSR (row_ptr[n+1],
+ * col_idx[nnz], with the rules of f2v_create, not re-checked here) and the
+ * two FP32 embedding buffers (n x d, row-major).  It computes, for the
+ * vertices u in [mb_begin, mb_end), the same update as a context's epoch
+ * `epoch` (negative samples from `seed`, learning rate `eta`): partner rows
+ * v < mb_begin are read from z_next (already updated this epoch) and all
+ * other rows, the minibatch's own included, from z_cur; the new rows are
+ * written to z_next[mb_begin..mb_end).  Other rows of z_next are untouched.
+ * A caller runs the minibatches of an epoch in order and then swaps the
+ * buffers.  Work is enqueued on `stream` (a cudaStream_t, may be NULL); the
+ * call waits on that stream once, to read the minibatch's pair count.
+ *
+ * Scratch lives in one fixed 8 MiB device array inside the library, which
+ * every device that loads the library keeps until the process exits.  A
+ * minibatch fits if about 8 * (mb_end - mb_begin + 33) + 4 * (mb_end -
+ * mb_begin) + (9 * d + 5) * ceil(pairs / 32) bytes stay within it (pairs =
+ * sum over the minibatch of max(deg(u) + s, 1)); for d = 128 that is about
+ * 7,000 pairs per 1 MiB, so a 4096-vertex minibatch of average degree 30
+ * fits.  Larger minibatches return F2V_EINVAL with the caller's buffers
+ * untouched.  All
+ * calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other host threads on the same device) race and give wrong
+ * results.  The first call on each device looks up the array's address with
+ * that device current; make it before any stream capture.  Errors are read
+ * with f2v_noalloc_last_error.
+ */
+f2v_status f2v_minibatch_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                                 int32_t d, f2v_model model, int32_t s, float eta, uint64_t seed,
+                                 int32_t epoch, int32_t mb_begin, int32_t mb_end,
+                                 const float *z_cur, float *z_next, void *stream);
+
+/* Message of the last f2v_minibatch_noalloc failure on this thread. */
+const char *f2v_noalloc_last_error(void);
+
 /* Message of the last failure on this context ("" if none). */
 const char *f2v_last_error(const f2v_ctx *ctx);
 

@@ -86,6 +86,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
             "f2v_set_kernel_timing": ([vp, i32], st),
             "f2v_read_kernel_timing": ([vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)], st),
+            "f2v_minibatch_noalloc": ([vp, vp, i32, i32, st, i32, f32, u64, i32, i32, i32, vp,
+                                       vp, vp], st),
+            "f2v_noalloc_last_error": ([], ctypes.c_char_p),
             "f2v_last_error": ([vp], ctypes.c_char_p),
             "f2v_last_error_global": ([], ctypes.c_char_p),
         }
