@@ -29,7 +29,8 @@ import numpy as np  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
-KERNEL_SOURCES = ["paper_2009_10035_gb300/csrc/f2v_force.cuh",
+KERNEL_SOURCES = ["paper_2009_10035_gb300/csrc/f2v_bulk.cuh",
+                  "paper_2009_10035_gb300/csrc/f2v_force.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_device.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_force_fp32.cu"]
 FALLBACK_HBM_GBS = 6800.0
@@ -298,7 +299,7 @@ def run_ours(args, g, world, rank, local):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
-                "kernel": "force_kernel<32,4,1,true,float> (fused SDDMM+SpMM+update)",
+                "kernel": "force_bulk_kernel<128, float> (TMA-staged fused SDDMM+SpMM+update)",
                 "per_launch": {"algorithmic_bytes": alg_bytes / (args.steps * M),
                                "avg_duration_us": 1e3 * kernel_ms / max(n_timed, 1),
                                "launches_timed": n_timed},
