@@ -141,6 +141,17 @@ struct f2v_ctx {
     int levels = 0;                        // combine-tree levels in use
     float *slots = nullptr;                // all levels, in order
     int32_t *unit_cnt = nullptr;
+    // staged (persistent) kernel only
+    int ring = 1;                          // combine-tree scratch regions
+    int64_t slot_stride = 0, cnt_stride = 0;   // elements between regions
+    int64_t *d_mb_item_base = nullptr;     // M + 1
+    int32_t *d_mb_C = nullptr;             // M
+    int32_t *row_flag = nullptr;           // n: epoch + 1 once written this epoch
+    int32_t *mb_done = nullptr;            // M: chunks finished in this launch
+    CUtensorMap zmap{};                    // both Z buffers: 2n rows of the storage type
+    CUtensorMap mmap{};                    // the FP32 master (BF16 form)
+    int32_t *partner = nullptr;            // partner code of every pair of an epoch
+    int partner_epoch = -1;                // epoch whose partners `partner` holds
     int cur = 0;                           // buffer holding Z as of the epoch's start
     int mb_pos = 0;                        // next minibatch of the current epoch
     size_t device_bytes = 0;
@@ -211,8 +222,11 @@ void release(f2v_ctx *c)
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     void *bufs[] = {c->err_word, c->row_ptr, c->col_idx, c->item_u0, c->counter, c->apair,
-                    c->z[0], c->z[1], c->master};
+                    c->z[0], c->master};
     for (void *p : bufs)
+        if (p) cudaFree(p);
+    void *bulk_bufs[] = {c->d_mb_item_base, c->d_mb_C, c->row_flag, c->mb_done, c->partner};
+    for (void *p : bulk_bufs)
         if (p) cudaFree(p);
     if (c->slots) cudaFree(c->slots);
     if (c->unit_cnt) cudaFree(c->unit_cnt);
@@ -406,56 +420,105 @@ void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
     a.err = c->err_word;
 }
 
-// Launches the force kernel of minibatch k of the current epoch.
-f2v_status run_minibatch(f2v_ctx *c, int k)
+template <typename Ts>
+void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochArgs<Ts> &ea)
+{
+    fill_args(c, k_begin, eta, ea.f);
+    ea.partner = c->partner;
+    ea.items = c->item_u0;
+    ea.mb_item_base = c->d_mb_item_base;
+    ea.mb_C = c->d_mb_C;
+    ea.row_flag = c->row_flag;
+    ea.mb_done = c->mb_done;
+    ea.slots = c->slots;
+    ea.unit_cnt = c->unit_cnt;
+    ea.slot_stride = c->slot_stride;
+    ea.cnt_stride = c->cnt_stride;
+    ea.k_begin = k_begin;
+    ea.k_end = k_end;
+    ea.b = c->b;
+    ea.ring = c->ring;
+    ea.zcur_row0 = c->cur * c->n;
+    ea.znext_row0 = (c->cur ^ 1) * c->n;
+    ea.own_row0 = (c->precision == F2V_BF16) ? 0 : c->cur * c->n;
+}
+
+// Launches the force kernel(s) for minibatches [k_begin, k_end) of the
+// current epoch: one persistent launch for the staged kernel, one launch
+// per minibatch for the register kernel.  Each launch is bracketed by timing
+// events when timing is on.
+f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
 {
     const int e = c->epoch;
     const float eta = (float)lr_for_epoch(c, e);
-    const int nxt = c->cur ^ 1;
-    const int u0 = k * c->b, u1 = std::min(c->n, u0 + c->b);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (c->timing) {
-        f2v_status st = get_event(c, &e0);
-        if (st == F2V_OK) st = get_event(c, &e1);
-        if (st != F2V_OK) return st;
-        F2V_CUDA(c, cudaEventRecord(e0, c->stream));
+    const int step = c->bulk ? (k_end - k_begin) : 1;
+    if (c->bulk && c->partner_epoch != e) {   // this epoch's partner list
+        cudaError_t ee = launch_expand_partners(
+            c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)e, (uint32_t)c->seed,
+            (uint32_t)(c->seed >> 32), c->partner, c->stream);
+        c->launches++;
+        if (ee != cudaSuccess)
+            return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
+        c->partner_epoch = e;
     }
-    cudaError_t err;
-    if (c->precision == F2V_BF16) {
-        ForceArgs<__nv_bfloat16> a{};
-        fill_args(c, k, eta, a);
-        a.master = c->master;
-        if (c->bulk)
-            err = launch_bulk_bf16(c->d, a, (a.n_items + c->bulk_warps - 1) / c->bulk_warps,
-                                   c->bulk_warps, c->bulk_smem, c->stream);
-        else
-            err = launch_force_bf16(c->shape, a, c->blocks_cap, c->stream);
-    } else {
-        ForceArgs<float> a{};
-        fill_args(c, k, eta, a);
-        a.master = nullptr;
-        if (c->bulk)
-            err = launch_bulk_fp32(c->d, a, (a.n_items + c->bulk_warps - 1) / c->bulk_warps,
-                                   c->bulk_warps, c->bulk_smem, c->stream);
-        else
-            err = launch_force_fp32(c->shape, a, c->blocks_cap, c->stream);
-    }
-    c->launches++;
-    if (err != cudaSuccess)
-        return fail(c, F2V_ECUDA, "force kernel launch (epoch %d, minibatch %d): %s", e, k,
-                    cudaGetErrorString(err));
-    if (c->timing) {
-        F2V_CUDA(c, cudaEventRecord(e1, c->stream));
-        c->ev_pending.push_back(e0);
-        c->ev_pending.push_back(e1);
+    if (c->bulk)
+        F2V_CUDA(c, cudaMemsetAsync(c->mb_done + k_begin, 0,
+                                    sizeof(int32_t) * (size_t)(k_end - k_begin), c->stream));
+    for (int k = k_begin; k < k_end; k += step) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->timing) {
+            f2v_status st = get_event(c, &e0);
+            if (st == F2V_OK) st = get_event(c, &e1);
+            if (st != F2V_OK) return st;
+            F2V_CUDA(c, cudaEventRecord(e0, c->stream));
+        }
+        cudaError_t err;
+        if (c->precision == F2V_BF16) {
+            if (c->bulk) {
+                EpochArgs<__nv_bfloat16> ea{};
+                fill_epoch_args(c, k, k + step, eta, ea);
+                ea.f.master = c->master;
+                err = launch_bulk_bf16(c->d, ea, c->zmap, c->mmap, c->bulk_sms, c->bulk_warps,
+                                       c->bulk_smem, c->stream);
+            } else {
+                ForceArgs<__nv_bfloat16> a{};
+                fill_args(c, k, eta, a);
+                a.master = c->master;
+                err = launch_force_bf16(c->shape, a, c->blocks_cap, c->stream);
+            }
+        } else {
+            if (c->bulk) {
+                EpochArgs<float> ea{};
+                fill_epoch_args(c, k, k + step, eta, ea);
+                ea.f.master = nullptr;
+                err = launch_bulk_fp32(c->d, ea, c->zmap, c->zmap, c->bulk_sms, c->bulk_warps,
+                                       c->bulk_smem, c->stream);
+            } else {
+                ForceArgs<float> a{};
+                fill_args(c, k, eta, a);
+                a.master = nullptr;
+                err = launch_force_fp32(c->shape, a, c->blocks_cap, c->stream);
+            }
+        }
+        c->launches++;
+        if (err != cudaSuccess)
+            return fail(c, F2V_ECUDA, "force kernel launch (epoch %d, minibatch %d): %s", e, k,
+                        cudaGetErrorString(err));
+        if (c->timing) {
+            F2V_CUDA(c, cudaEventRecord(e1, c->stream));
+            c->ev_pending.push_back(e0);
+            c->ev_pending.push_back(e1);
+        }
     }
     return F2V_OK;
 }
 
-// Advances the minibatch position; at the end of an epoch the buffers swap.
-void advance(f2v_ctx *c)
+// Advances the minibatch position by `count` within the epoch; at the end
+// of an epoch the buffers swap.
+void advance(f2v_ctx *c, int count)
 {
-    if (++c->mb_pos == num_minibatches(c)) {
+    c->mb_pos += count;
+    if (c->mb_pos == num_minibatches(c)) {
         c->mb_pos = 0;
         c->cur ^= 1;
         c->epoch++;
@@ -465,11 +528,11 @@ void advance(f2v_ctx *c)
 // Runs the remaining minibatches of the current epoch.
 f2v_status run_epoch(f2v_ctx *c)
 {
-    do {
-        f2v_status st = run_minibatch(c, c->mb_pos);
-        if (st != F2V_OK) return st;
-        advance(c);
-    } while (c->mb_pos != 0);
+    const int M = num_minibatches(c);
+    const int k0 = c->mb_pos;
+    f2v_status st = run_range(c, k0, M);
+    if (st != F2V_OK) return st;
+    advance(c, M - k0);
     return F2V_OK;
 }
 
@@ -549,10 +612,14 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
     sms = std::max(sms, 1);
     c->blocks_cap = sms * 8;
-    if (!(flags & F2V_FLAG_NO_STAGING) &&
-        bulk_config(d, precision == F2V_BF16, &c->bulk_warps, &c->bulk_smem)) {
+    // the staged kernel is persistent: its grid (one block per SM) must fit
+    if (!(flags & F2V_FLAG_NO_STAGING) && n < (1 << 30) &&   // map rows (2n) are int32
+
+        bulk_config(d, precision == F2V_BF16, &c->bulk_warps, &c->bulk_smem) &&
+        bulk_resident(d, precision == F2V_BF16, c->bulk_warps, c->bulk_smem) >= 1) {
         c->bulk = true;
         c->bulk_sms = sms;
+        c->ring = 4;
     }
 
     std::vector<int32_t> items;
@@ -577,8 +644,9 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
     if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
     if (st == F2V_OK) st = alloc(c, (void **)&c->item_u0, sizeof(int32_t) * items.size());
     if (st == F2V_OK) st = alloc(c, (void **)&c->counter, sizeof(int32_t) * (size_t)n);
-    if (st == F2V_OK) st = alloc(c, &c->z[0], zbytes);
-    if (st == F2V_OK) st = alloc(c, &c->z[1], zbytes);
+    // both Z buffers in one allocation: one TMA map then covers either
+    if (st == F2V_OK) st = alloc(c, &c->z[0], 2 * zbytes);
+    if (st == F2V_OK) c->z[1] = static_cast<char *>(c->z[0]) + zbytes;
     if (st == F2V_OK && precision == F2V_BF16)
         st = alloc(c, (void **)&c->master, (size_t)n * c->ld * sizeof(float));
     // combine tree: level l has ceil(max_items / 16^l) units, two slots each
@@ -594,11 +662,32 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
             if (units <= 1 || c->levels == kMaxLevels) break;
             units = (units + kFan - 1) / kFan;
         }
-        st = alloc(c, (void **)&c->slots, sizeof(float) * (size_t)c->ld * slot_rows);
-        if (st == F2V_OK) st = alloc(c, (void **)&c->unit_cnt, sizeof(int32_t) * (counters + 1));
+        // the persistent kernel keeps `ring` regions, one per minibatch in flight
+        c->slot_stride = (int64_t)c->ld * (int64_t)slot_rows;
+        c->cnt_stride = (int64_t)counters + 1;
+        const size_t ring = (size_t)c->ring;
+        st = alloc(c, (void **)&c->slots, sizeof(float) * (size_t)c->slot_stride * ring);
+        if (st == F2V_OK)
+            st = alloc(c, (void **)&c->unit_cnt, sizeof(int32_t) * (size_t)c->cnt_stride * ring);
         if (st == F2V_OK &&
-            cudaMemsetAsync(c->unit_cnt, 0, sizeof(int32_t) * (counters + 1), c->stream) != cudaSuccess)
+            cudaMemsetAsync(c->unit_cnt, 0, sizeof(int32_t) * (size_t)c->cnt_stride * ring,
+                            c->stream) != cudaSuccess)
             st = fail(c, F2V_ECUDA, "memset of combine counters failed");
+    }
+    if (st == F2V_OK && c->bulk) {
+        const size_t M = c->mb_C.size();
+        st = alloc(c, (void **)&c->d_mb_item_base, sizeof(int64_t) * (M + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->row_flag, sizeof(int32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * M);
+        if (st == F2V_OK)
+            st = alloc(c, (void **)&c->partner, sizeof(int32_t) * (size_t)c->h_apair[(size_t)n]);
+        std::string merr;
+        if (st == F2V_OK &&
+            (!make_row_map(&c->zmap, c->z[0], 2 * (int64_t)n, d, precision == F2V_BF16, &merr) ||
+             (precision == F2V_BF16 &&
+              !make_row_map(&c->mmap, c->master, (int64_t)n, d, false, &merr))))
+            st = fail(c, F2V_ECUDA, "tensor map: %s", merr.c_str());
     }
     if (st != F2V_OK) {
         g_last_error = c->err;
@@ -628,6 +717,15 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
                                     cudaMemcpyHostToDevice, c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(int32_t) * (size_t)n, c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(int32_t), c->stream));
+    if (c->bulk) {
+        const size_t M = c->mb_C.size();
+        CREATE_CUDA(cudaMemcpyAsync(c->d_mb_item_base, c->mb_item_base.data(),
+                                    sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, c->stream));
+        CREATE_CUDA(cudaMemcpyAsync(c->d_mb_C, c->mb_C.data(), sizeof(int32_t) * M,
+                                    cudaMemcpyHostToDevice, c->stream));
+        CREATE_CUDA(cudaMemsetAsync(c->row_flag, 0, sizeof(int32_t) * (size_t)n, c->stream));
+        CREATE_CUDA(cudaMemsetAsync(c->mb_done, 0, sizeof(int32_t) * M, c->stream));
+    }
     CREATE_CUDA(launch_init(c));
     CREATE_CUDA(cudaStreamSynchronize(c->stream));
 #undef CREATE_CUDA
@@ -667,10 +765,14 @@ f2v_status f2v_run_minibatches(f2v_ctx *ctx, int32_t count)
     F2V_CHECK_CTX(ctx);
     if (count < 0) return fail(ctx, F2V_EINVAL, "count = %d < 0", count);
     DeviceGuard g(ctx->device);
-    for (int32_t i = 0; i < count; ++i) {
-        f2v_status st = run_minibatch(ctx, ctx->mb_pos);
+    const int M = num_minibatches(ctx);
+    while (count > 0) {
+        const int k0 = ctx->mb_pos;
+        const int k1 = std::min(M, k0 + count);
+        f2v_status st = run_range(ctx, k0, k1);
         if (st != F2V_OK) return st;
-        advance(ctx);
+        advance(ctx, k1 - k0);
+        count -= k1 - k0;
     }
     return F2V_OK;
 }
@@ -705,7 +807,7 @@ f2v_status f2v_get_embedding(f2v_ctx *ctx, float *out, size_t count)
     F2V_CUDA(ctx, cudaMemcpyAsync(out, src, want * sizeof(float), cudaMemcpyDeviceToHost,
                                   ctx->stream));
     F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    return F2V_OK;
+    return check_device_error(ctx);
 }
 
 f2v_status f2v_get_embedding_device(f2v_ctx *ctx, float *dev_out, size_t count)
@@ -779,6 +881,11 @@ f2v_status f2v_set_epoch(f2v_ctx *ctx, int32_t epoch)
     DeviceGuard g(ctx->device);
     f2v_status st = sync_current(ctx);
     if (st != F2V_OK) return st;
+    // row flags name the epoch a row was written in; a counter that moves
+    // (backwards, or to an epoch run before) must not meet stale flags
+    if (ctx->row_flag)
+        F2V_CUDA(ctx, cudaMemsetAsync(ctx->row_flag, 0, sizeof(int32_t) * (size_t)ctx->n,
+                                      ctx->stream));
     ctx->mb_pos = 0;
     ctx->epoch = epoch;
     return F2V_OK;

@@ -1,26 +1,37 @@
-// f2v_bulk.cuh -- the force+update kernel for row sizes d = 32 * EPL
-// (EPL = 2, 4, 8), with partner rows staged in shared memory by TMA bulk
-// copies instead of register gathers.
+// f2v_bulk.cuh -- the persistent force+update kernel for row sizes
+// d = 32 * EPL (EPL = 2, 4, 8), with partner rows staged in shared memory by
+// TMA bulk copies.  One launch runs a range of minibatches of one epoch.
 //
-// One warp walks one contiguous chunk of the minibatch's pair sequence (the
-// same pair order as the register kernel: neighbours in CSR order, then the
-// s negative samples).  Per tile of at most 32 pairs spanning at most 8
-// vertices:
+// Work.  Minibatch k's pair sequence (neighbours of each vertex in CSR
+// order, then its s negative samples) is cut into one contiguous chunk per
+// warp; warp w takes chunk w of every minibatch, in minibatch order, and
+// flows from one minibatch into the next without a grid-wide barrier.  Per
+// tile of at most 32 pairs spanning at most 8 vertices:
 //   decode  lane t finds pair t's vertex and partner (col_idx or Philox);
 //   stage   lane t issues one cp.async.bulk copy of its partner row into the
 //           warp's shared buffer, lanes j < 8 copy the tile's own rows, all
-//           completing on one mbarrier; the next tile is decoded while the
-//           copies are in flight;
+//           completing on one mbarrier; the next tile (possibly of the next
+//           minibatch) is decoded while the copies are in flight;
 //   reduce  each lane forms the partial dot product / squared distance of
 //           all 32 rows over its EPL elements, and a transpose-reduction
 //           (31 shuffles) leaves lane r with row r's full sum;
 //   force   lane r turns its sum into the scalar of Eq. 5/6 or Eq. 8/9;
 //   update  rows are accumulated per vertex in registers; a vertex that
-//           ends is written (z_u - eta g, Eq. 10) or, if it began in an
-//           earlier chunk or runs into a later one, passed up the ordered
-//           combine tree of f2v_internal.h with chunks as level-0 units.
-// Waits on the mbarrier are bounded: after about a second the kernel records
-// an error code, waits (bounded again) for its copies, and stops.
+//           ends is written (z_u - eta g, Eq. 10) or, if it spans several
+//           chunks, passed up the ordered combine tree of f2v_internal.h.
+//
+// Ordering between minibatches (synchronous SGD, Sec. III-B).  A partner row
+// v of an earlier minibatch is read from the next buffer only after its
+// flag row_flag[v] equals epoch + 1, which its writer releases after the row
+// is stored.  A warp checks those flags only after finishing its own chunk
+// of the previous minibatch, so the warp on the oldest minibatch always
+// progresses.  The combine-tree scratch is a ring of `ring` regions; before
+// starting minibatch k a warp waits until minibatch k - ring is complete.
+// All warps of the grid must be resident at once (one block per SM).
+//
+// Every wait is bounded (about a second at 2 GHz): on expiry the kernel
+// records an error code (1 mbarrier, 2 row flag, 3 ring), lets its own copies
+// land, and returns; the host reports F2V_ETIMEOUT.
 #pragma once
 
 #include <climits>
@@ -31,7 +42,8 @@
 
 namespace f2v {
 
-constexpr int kOwnSlots = 8;            // distinct vertices per tile at most
+constexpr int kOwnSlots = 8;                 // distinct vertices per tile at most
+constexpr long long kWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -75,9 +87,27 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         : "memory");
 }
 
+// TMA tile::gather4: rows r0..r3 (each one box = one whole row) of the 2-D
+// tensor behind `map` into consecutive rows at dst, completing on `bar`.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, int r0, int r1,
+                                            int r2, int r3, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1),
+          "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 __device__ __forceinline__ void fence_mbar_init()
@@ -85,13 +115,44 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait (about a second at 2 GHz); false on time-out.
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait on an mbarrier phase; false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+// Bounded wait until *p >= target (acquire); false on time-out.
+__device__ __forceinline__ bool wait_at_least(const int32_t *p, int target)
+{
+    if (ld_acquire(p) >= target) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(p) < target) {
+        if (clock64() - t0 > kWaitCycles) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Bounded wait until *p == target (acquire); false on time-out.
+__device__ __forceinline__ bool wait_equal(const int32_t *p, int target)
+{
+    if (ld_acquire(p) == target) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(p) != target) {
+        if (clock64() - t0 > kWaitCycles) return false;
+        __nanosleep(32);
     }
     return true;
 }
@@ -106,13 +167,45 @@ struct BulkLayout {
     static constexpr int COEF_OFF = OWN_OFF + kOwnSlots * OWNB;    // float[32]
     static constexpr int VERT_OFF = COEF_OFF + 32 * 4;             // int[32]: vertex - u_tile
     static constexpr int VEND_OFF = VERT_OFF + 32 * 4;             // int[32]: vertex end
-    static constexpr int KIND_OFF = VEND_OFF + 32 * 4;             // int[32]
-    static constexpr int BAR_OFF = KIND_OFF + 32 * 4;              // uint64
+    static constexpr int BAR_OFF = VEND_OFF + 32 * 4;              // uint64
     static constexpr int BYTES = ((BAR_OFF + 8 + 127) / 128) * 128;
 };
 
-// Lane-parallel decode of the tile starting at pair q (local), within the
-// chunk ending at q_end, whose first pair lies in vertex u.
+// One chunk of one minibatch.
+struct Chunk {
+    int k;                 // minibatch
+    int mb_begin;          // its first vertex
+    int64_t P0;            // its first pair (global index)
+    int q_begin, q_end;    // the chunk's pairs, local to the minibatch
+    int C;                 // pairs per chunk in this minibatch
+    int u0;                // vertex holding pair q_begin
+};
+
+// First chunk of warp w in a minibatch >= k of the launch; false if none.
+template <typename Ts>
+__device__ __forceinline__ bool find_chunk(const EpochArgs<Ts> &a, int w, int k, Chunk &c)
+{
+    for (; k < a.k_end; ++k) {
+        const int64_t base = __ldg(&a.mb_item_base[k]);
+        const int64_t nch = __ldg(&a.mb_item_base[k + 1]) - base;
+        if (w < nch) {
+            c.k = k;
+            c.mb_begin = k * a.b;
+            const int mb_end = min(a.f.n, c.mb_begin + a.b);
+            c.P0 = __ldg(&a.f.apair[c.mb_begin]);
+            const int Pk = (int)(__ldg(&a.f.apair[mb_end]) - c.P0);
+            c.C = __ldg(&a.mb_C[k]);
+            c.q_begin = w * c.C;
+            c.q_end = min(c.q_begin + c.C, Pk);
+            c.u0 = __ldg(&a.items[base + w]);
+            return true;
+        }
+    }
+    return false;
+}
+
+// Lane-parallel decode of the tile starting at pair q (local to the chunk's
+// minibatch), within the chunk, whose first pair lies in vertex u.
 struct Tile {
     int q, n, u;          // first pair, pairs in the tile, vertex of the first pair
     int nverts;           // distinct vertices in the tile (<= kOwnSlots)
@@ -120,25 +213,28 @@ struct Tile {
     int first_lo;         // start of vertex u (local pair index)
     // per lane (pair q + lane)
     int pu, nb, kind, p_hi;
+    bool ready;           // partner row may be read now
 };
 
 template <typename Ts>
-__device__ __forceinline__ Tile decode_tile(const ForceArgs<Ts> &a, int q, int q_end, int u,
-                                            int lane)
+__device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk &ch, int q,
+                                            int u, int lane)
 {
     Tile t;
     t.q = q;
     t.u = u;
+    const int q_end = ch.q_end;
     const int uu = u + lane;
-    int A_hi = INT_MAX, rp_lo = 0, rp_hi = 0;
-    if (uu < a.n) {
-        const int64_t ah = __ldg(&a.apair[uu + 1]) - a.P0;
+    // two independent loads per lane: the end of vertex u + lane, and the
+    // partner code of pair q + lane
+    int A_hi = INT_MAX;
+    if (uu < a.f.n) {
+        const int64_t ah = __ldg(&a.f.apair[uu + 1]) - ch.P0;
         A_hi = ah > INT_MAX ? INT_MAX : (int)ah;
-        rp_lo = __ldg(&a.row_ptr[uu]);
-        rp_hi = __ldg(&a.row_ptr[uu + 1]);
     }
+    const int code = (q + lane < q_end) ? __ldg(&a.partner[ch.P0 + q + lane]) : kPartnerNone;
     const int A_up = __shfl_up_sync(0xffffffffu, A_hi, 1);
-    const int A_lo = (lane == 0) ? (int)(__ldg(&a.apair[u]) - a.P0) : A_up;
+    const int A_lo = (lane == 0) ? (int)(__ldg(&a.f.apair[u]) - ch.P0) : A_up;
     t.first_lo = __shfl_sync(0xffffffffu, A_lo, 0);
     // at most 32 pairs, at most kOwnSlots vertices, not past the chunk
     const int end8 = __shfl_sync(0xffffffffu, A_hi, kOwnSlots - 1);
@@ -148,24 +244,21 @@ __device__ __forceinline__ Tile decode_tile(const ForceArgs<Ts> &a, int q, int q
     const unsigned ends = __reduce_or_sync(0xffffffffu, bit);
     const int off = __popc(ends & ((2u << lane) - 1u));
     t.pu = u + off;
-    const int pA_lo = __shfl_sync(0xffffffffu, A_lo, off);
     t.p_hi = __shfl_sync(0xffffffffu, A_hi, off);
-    const int prp_lo = __shfl_sync(0xffffffffu, rp_lo, off);
-    const int prp_hi = __shfl_sync(0xffffffffu, rp_hi, off);
     t.nb = t.pu;
     t.kind = KIND_NONE;
+    t.ready = true;
     if (lane < t.n) {
-        const int j = q + lane - pA_lo;
-        const int deg = prp_hi - prp_lo;
-        if (j < deg) {
-            t.nb = __ldg(&a.col_idx[prp_lo + j]);
+        if (code >= 0) {
+            t.nb = code;
             t.kind = KIND_ATTR;
-        } else if (j - deg < a.s) {
-            const uint32_t x0 =
-                philox_x0((uint32_t)t.pu, a.epoch, (uint32_t)(j - deg), 0u, a.key0, a.key1);
-            t.nb = (int)(x0 % (uint32_t)a.n);
-            t.kind = (t.nb == t.pu) ? KIND_NONE : KIND_REP;
+        } else if (code != kPartnerNone) {
+            t.nb = -2 - code;
+            t.kind = KIND_REP;
         }
+        // a row of an earlier minibatch: readable once its writer released it
+        if (t.kind != KIND_NONE && t.nb < ch.mb_begin)
+            t.ready = ld_acquire(&a.row_flag[t.nb]) == (int)a.f.epoch + 1;
     }
     t.nverts = __shfl_sync(0xffffffffu, off, t.n - 1) + 1;
     t.u_next = u + __popc(__ballot_sync(0xffffffffu, pos <= t.n));
@@ -173,7 +266,10 @@ __device__ __forceinline__ Tile decode_tile(const ForceArgs<Ts> &a, int q, int q
 }
 
 template <int D, typename Ts>
-__global__ void __launch_bounds__(D <= 64 ? 512 : 320) force_bulk_kernel(const ForceArgs<Ts> a)
+__global__ void __launch_bounds__(D <= 64 ? 512 : 320)
+    force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
+                      const __grid_constant__ CUtensorMap zmap,
+                      const __grid_constant__ CUtensorMap mmap)
 {
     using Lay = BulkLayout<D, Ts>;
     constexpr int EPL = D / 32;                     // elements per lane
@@ -184,15 +280,16 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320) force_bulk_kernel(const F
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
+    const int w = blockIdx.x * warps + warp;        // this warp's chunk in every minibatch
     unsigned char *wsm = smem_raw + (size_t)warp * Lay::BYTES;
     Ts *rows = reinterpret_cast<Ts *>(wsm + Lay::ROWS_OFF);
     float *own = reinterpret_cast<float *>(wsm + Lay::OWN_OFF);
     float *coefs = reinterpret_cast<float *>(wsm + Lay::COEF_OFF);
     int *vert = reinterpret_cast<int *>(wsm + Lay::VERT_OFF);
     int *vends = reinterpret_cast<int *>(wsm + Lay::VEND_OFF);
-    int *kinds = reinterpret_cast<int *>(wsm + Lay::KIND_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + Lay::BAR_OFF);
-    const bool tdist = (a.model == 0);
+    const bool tdist = (a.f.model == 0);
+    const int flag_value = (int)a.f.epoch + 1;
 
     // zero the staging buffers once, so rows that are never copied are finite
     {
@@ -206,65 +303,133 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320) force_bulk_kernel(const F
     __syncwarp();
     uint32_t phase = 0;
 
-    for (int chunk = blockIdx.x * warps + warp; chunk < a.n_items; chunk += gridDim.x * warps) {
-        const int q_begin = chunk * a.C;
-        const int q_end = min(q_begin + a.C, a.Pk);
-        const int u0 = __ldg(&a.item_u0[chunk]);
-        Tile t = decode_tile(a, q_begin, q_end, u0, lane);
-        int ucur = -1, vbeg = 0, vend = 0;
-        float zu[EPL], g[EPL];
+    Chunk ch;
+    if (!find_chunk(a, w, a.k_begin, ch)) return;
+    Tile t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
+    bool chunk_start = true;
+    int ucur = -1, vbeg = 0, vend = 0;
+    float zu[EPL], g[EPL];
 #pragma unroll
-        for (int e = 0; e < EPL; ++e) { zu[e] = 0.f; g[e] = 0.f; }
+    for (int e = 0; e < EPL; ++e) { zu[e] = 0.f; g[e] = 0.f; }
 
-        while (true) {
-            // ---- stage the tile: partner rows and own rows, one mbarrier --
-            const int myvert = (lane < t.n) ? t.pu - t.u : 0;
-            vert[lane] = myvert;
-            vends[lane] = t.p_hi;
-            const bool has_row = (lane < t.n) && (t.kind != KIND_NONE);
-            const bool has_own = lane < t.nverts;
-            const uint32_t bytes =
-                (uint32_t)__popc(__ballot_sync(0xffffffffu, has_row)) * Lay::ROWB +
-                (uint32_t)t.nverts * Lay::OWNB;
-            // rows where a new vertex segment begins
-            const int prev_vert = __shfl_up_sync(0xffffffffu, myvert, 1);
-            const unsigned seg_starts =
-                __ballot_sync(0xffffffffu, lane < t.n && (lane == 0 || prev_vert != myvert));
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (has_row) {
-                const Ts *src = ((t.nb < a.mb_begin) ? a.znext : a.zcur) + (int64_t)t.nb * a.ld;
-                bulk_copy_g2s(rows + lane * D, src, Lay::ROWB, bar);
+    while (true) {
+        // ---- minibatch entry: the scratch region must be free ------------
+        if (chunk_start) {
+            chunk_start = false;
+            if (ch.k - a.ring >= a.k_begin) {
+                const int kk = ch.k - a.ring;
+                const int target =
+                    (int)(__ldg(&a.mb_item_base[kk + 1]) - __ldg(&a.mb_item_base[kk]));
+                int ok = 1;
+                if (lane == 0) ok = wait_at_least(&a.mb_done[kk], target);
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    if (lane == 0) atomicExch(a.f.err, 3);
+                    return;
+                }
             }
-            if (has_own) {
-                const int w = t.u + lane;
-                const float *src = (sizeof(Ts) == 2) ? a.master + (int64_t)w * a.ld
-                                                     : reinterpret_cast<const float *>(a.zcur) +
-                                                           (int64_t)w * a.ld;
-                bulk_copy_g2s(own + lane * D, src, Lay::OWNB, bar);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
-            const int tn = t.n, tu = t.u, tq = t.q, first_lo = t.first_lo;
-            const int tkind = (lane < t.n) ? t.kind : KIND_NONE;
-
-            // ---- decode the next tile while the copies are in flight ------
-            const int q_next = tq + tn;
-            const bool more = q_next < q_end;
-            if (more) t = decode_tile(a, q_next, q_end, t.u_next, lane);
-
-            if (!mbar_wait_bounded(bar, phase)) {
-                if (lane == 0) atomicExch(a.err, 1);
-                mbar_wait_bounded(bar, phase);      // let the copies land before leaving
+        }
+        // ---- rows of earlier minibatches: wait until written ------------
+        const bool has_row = (lane < t.n) && (t.kind != KIND_NONE);
+        if (__any_sync(0xffffffffu, has_row && !t.ready)) {
+            int ok = 1;
+            if (has_row && !t.ready) ok = wait_equal(&a.row_flag[t.nb], flag_value);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) atomicExch(a.f.err, 2);
                 return;
             }
-            phase ^= 1u;
-            __syncwarp();
+        }
+        // rows written in this launch are read through the async proxy next
+        if (__any_sync(0xffffffffu, has_row && t.nb < ch.mb_begin)) fence_proxy_async_global();
 
-            // ---- reduce: partial sums of all 32 rows (rows past the tile and
-            // rows without a copy hold finite stale data and are discarded),
-            // then a transpose-reduction leaves row r's sum in lane r.
-            float p[32];
+        // ---- stage the tile: partner rows and own rows, one mbarrier -----
+        const int myvert = (lane < t.n) ? t.pu - t.u : 0;
+        vert[lane] = myvert;
+        vends[lane] = t.p_hi;
+        // map row of each lane's partner (a finite stand-in where there is none)
+        const int prow = has_row ? t.nb + ((t.nb < ch.mb_begin) ? a.znext_row0 : a.zcur_row0)
+                                 : a.zcur_row0 + t.u;
+        const int ngroups = (t.n + 3) >> 2;          // gather4 loads of partner rows
+        const int nown = (t.nverts + 3) >> 2;        // gather4 loads of own rows (<= 2)
+        const uint32_t bytes = (uint32_t)ngroups * 4u * Lay::ROWB + (uint32_t)nown * 4u * Lay::OWNB;
+        int r4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r4[i] = __shfl_sync(0xffffffffu, prow, (4 * lane + i) & 31);
+        // rows where a new vertex segment begins
+        const int prev_vert = __shfl_up_sync(0xffffffffu, myvert, 1);
+        const unsigned seg_starts =
+            __ballot_sync(0xffffffffu, lane < t.n && (lane == 0 || prev_vert != myvert));
+        // The copies below overwrite the buffers the previous tile was read
+        // from.  No proxy fence is needed for that: a warp issues in order,
+        // and every shared-memory read of the previous tile fed an arithmetic
+        // instruction issued before this point, so it had returned its value.
+        __syncwarp();
+        if (lane < ngroups) {
+            tma_gather4(rows + 4 * lane * D, &zmap, r4[0], r4[1], r4[2], r4[3], bar);
+        } else if (lane >= 8 && lane < 8 + nown) {
+            int o4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                o4[i] = a.own_row0 + t.u + min(4 * (lane - 8) + i, t.nverts - 1);
+            tma_gather4(own + 4 * (lane - 8) * D, &mmap, o4[0], o4[1], o4[2], o4[3], bar);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(bar, bytes);
+        const int tn = t.n, tu = t.u, tq = t.q, first_lo = t.first_lo;
+        const int tkind = (lane < t.n) ? t.kind : KIND_NONE;
+        const Chunk cur = ch;
+
+        // ---- decode the next tile (maybe of the next minibatch) ----------
+        const int q_next = tq + tn;
+        const bool last_of_chunk = q_next >= cur.q_end;
+        bool more = true;
+        if (!last_of_chunk) {
+            t = decode_tile(a, cur, q_next, t.u_next, lane);
+        } else if (find_chunk(a, w, cur.k + 1, ch)) {
+            t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
+        } else {
+            more = false;
+        }
+
+        if (!mbar_wait_bounded(bar, phase)) {
+            if (lane == 0) atomicExch(a.f.err, 1);
+            mbar_wait_bounded(bar, phase);      // let the copies land before leaving
+            return;
+        }
+        phase ^= 1u;
+        __syncwarp();
+
+        // ---- reduce: partial sums of all 32 rows (rows past the tile and
+        // rows without a copy hold finite stale data and are discarded),
+        // then a transpose-reduction leaves row r's sum in lane r.
+        // A full tile of one vertex (most pairs live in such tiles) takes a
+        // path without per-row vertex lookups or predicates.
+        const bool single = (tn == 32) && (seg_starts == 1u);
+        float p[32];
+        if (single) {
+            float o[EPL];
+#pragma unroll
+            for (int i = 0; i < NV; ++i)
+                load_vec_smem<VEC>(own + (i * L + lane) * VEC, o + i * VEC);
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                float x[EPL];
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    load_vec_smem<VEC>(rows + r * D + (i * L + lane) * VEC, x + i * VEC);
+                float acc = 0.f;
+                if (tdist) {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) {
+                        const float df = o[e] - x[e];
+                        acc = fmaf(df, df, acc);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EPL; ++e) acc = fmaf(o[e], x[e], acc);
+                }
+                p[r] = acc;
+            }
+        } else {
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const int j = vert[r];
@@ -288,57 +453,85 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320) force_bulk_kernel(const F
                 }
                 p[r] = acc;
             }
+        }
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-                const bool upper = (lane & m) != 0;
+        for (int m = 16; m >= 1; m >>= 1) {
+            const bool upper = (lane & m) != 0;
 #pragma unroll
-                for (int i = 0; i < m; ++i) {
-                    const float send = upper ? p[i] : p[i + m];
-                    const float keep = upper ? p[i + m] : p[i];
-                    p[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            for (int i = 0; i < m; ++i) {
+                const float send = upper ? p[i] : p[i + m];
+                const float keep = upper ? p[i + m] : p[i];
+                p[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            }
+        }
+        // ---- force: lane r turns row r's sum into its pair's scalar -------
+        {
+            const float sdot = p[0];
+            float coef = 0.f;
+            if (tkind != KIND_NONE) {
+                if (tdist) {
+                    if (tkind == KIND_ATTR) {
+                        coef = 2.f / (1.f + sdot);                 // Eq. 8 / t
+                    } else {
+                        const float q2 = fmaxf(sdot, kT2Floor);
+                        coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
+                    }
+                } else {
+                    coef = (tkind == KIND_ATTR) ? -1.f / (1.f + expf(sdot))   // Eq. 5
+                                                : 1.f / (1.f + expf(-sdot));  // Eq. 6
                 }
             }
-            // ---- force: lane r turns row r's sum into its pair's scalar -----
-            {
-                const float sdot = p[0];
-                float coef = 0.f;
-                if (tkind != KIND_NONE) {
+            coefs[lane] = coef;              // 0 for pairs without a force
+        }
+        __syncwarp();
+
+        // ---- accumulate each vertex segment; finish vertices that end -----
+        const int ring_slot = cur.k % a.ring;
+        const FinishCtx fc{cur.C, a.slots + (int64_t)ring_slot * a.slot_stride,
+                           a.unit_cnt + (int64_t)ring_slot * a.cnt_stride, a.row_flag,
+                           flag_value};
+        unsigned starts = seg_starts;
+        while (starts) {
+            const int rs = __ffs(starts) - 1;
+            starts &= starts - 1;
+            const int re = starts ? __ffs(starts) - 1 : tn;
+            const int j = vert[rs];
+            if (tu + j != ucur) {
+                if (ucur >= 0)
+                    finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, w, ucur, vbeg,
+                                                     vend, zu, g);
+                vbeg = (ucur >= 0) ? vend : first_lo;
+                ucur = tu + j;
+                vend = vends[rs];
+#pragma unroll
+                for (int i = 0; i < NV; ++i)
+                    load_vec_smem<VEC>(own + j * D + (i * L + lane) * VEC, zu + i * VEC);
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) g[e] = 0.f;
+            }
+            // two accumulators (even and odd rows of each group of four) keep
+            // two independent FMA chains per element; added in a fixed order
+            float g2[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) g2[e] = 0.f;
+            if (single) {
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const float c = coefs[r];
+                    float x[EPL];
+#pragma unroll
+                    for (int k = 0; k < NV; ++k)
+                        load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
+                    float *acc = (r & 1) ? g2 : g;
                     if (tdist) {
-                        if (tkind == KIND_ATTR) {
-                            coef = 2.f / (1.f + sdot);                 // Eq. 8 / t
-                        } else {
-                            const float q2 = fmaxf(sdot, kT2Floor);
-                            coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
-                        }
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, zu[e] - x[e], acc[e]);
                     } else {
-                        coef = (tkind == KIND_ATTR) ? -1.f / (1.f + expf(sdot))   // Eq. 5
-                                                    : 1.f / (1.f + expf(-sdot));  // Eq. 6
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
                     }
                 }
-                coefs[lane] = coef;              // 0 for pairs without a force
-            }
-            __syncwarp();
-
-            // ---- accumulate each vertex segment; finish vertices that end ---
-            unsigned starts = seg_starts;
-            while (starts) {
-                const int rs = __ffs(starts) - 1;
-                starts &= starts - 1;
-                const int re = starts ? __ffs(starts) - 1 : tn;
-                const int j = vert[rs];
-                if (tu + j != ucur) {
-                    if (ucur >= 0)
-                        finish_vertex<32, VEC, NV, true>(a, 0xffffffffu, lane, chunk, ucur, vbeg,
-                                                         vend, zu, g);
-                    vbeg = (ucur >= 0) ? vend : first_lo;
-                    ucur = tu + j;
-                    vend = vends[rs];
-#pragma unroll
-                    for (int i = 0; i < NV; ++i)
-                        load_vec_smem<VEC>(own + j * D + (i * L + lane) * VEC, zu + i * VEC);
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) g[e] = 0.f;
-                }
+            } else {
                 for (int r0 = rs; r0 < re; r0 += 4) {
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
@@ -348,21 +541,34 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320) force_bulk_kernel(const F
 #pragma unroll
                         for (int k = 0; k < NV; ++k)
                             load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
+                        float *acc = (i & 1) ? g2 : g;
                         if (tdist) {
 #pragma unroll
-                            for (int e = 0; e < EPL; ++e) g[e] = fmaf(c, zu[e] - x[e], g[e]);
+                            for (int e = 0; e < EPL; ++e)
+                                acc[e] = fmaf(c, zu[e] - x[e], acc[e]);
                         } else {
 #pragma unroll
-                            for (int e = 0; e < EPL; ++e) g[e] = fmaf(c, x[e], g[e]);
+                            for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
                         }
                     }
                 }
             }
-            __syncwarp();
-            if (!more) break;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) g[e] += g2[e];
         }
-        if (ucur >= 0)
-            finish_vertex<32, VEC, NV, true>(a, 0xffffffffu, lane, chunk, ucur, vbeg, vend, zu, g);
+        if (last_of_chunk) {
+            // the chunk's last vertex, then the chunk counts as done
+            finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, w, ucur, vbeg, vend, zu,
+                                             g);
+            ucur = -1;
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(&a.mb_done[cur.k])
+                             : "memory");
+            chunk_start = true;
+        }
+        __syncwarp();
+        if (!more) break;
     }
 }
 
@@ -387,30 +593,52 @@ bool bulk_config_t(int d, int *warps, int *smem)
     }
 }
 
+// Blocks of `warps` warps that fit on one SM at once (0 if none).
 template <int D, typename Ts>
-cudaError_t launch_bulk_d(const ForceArgs<Ts> &a, int blocks, int warps, int smem,
-                          cudaStream_t st)
+int bulk_resident_d(int warps, int smem)
 {
-    static bool attr_set = false;          // per instantiation; set once per process
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    force_bulk_kernel<D, Ts><<<blocks, warps * 32, smem, st>>>(a);
+    if (cudaFuncSetAttribute(force_bulk_kernel<D, Ts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+        return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, force_bulk_kernel<D, Ts>,
+                                                      warps * 32, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+template <int D, typename Ts>
+cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const CUtensorMap &mmap,
+                          int blocks, int warps, int smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    force_bulk_kernel<D, Ts><<<blocks, warps * 32, smem, st>>>(a, zmap, mmap);
     return cudaGetLastError();
 }
 
 template <typename Ts>
-cudaError_t launch_bulk_t(int d, const ForceArgs<Ts> &a, int blocks, int warps, int smem,
+cudaError_t launch_bulk_t(int d, const EpochArgs<Ts> &a, const CUtensorMap &zmap,
+                          const CUtensorMap &mmap, int blocks, int warps, int smem,
                           cudaStream_t st)
 {
     switch (d) {
-        case 64: return launch_bulk_d<64, Ts>(a, blocks, warps, smem, st);
-        case 128: return launch_bulk_d<128, Ts>(a, blocks, warps, smem, st);
-        case 256: return launch_bulk_d<256, Ts>(a, blocks, warps, smem, st);
+        case 64: return launch_bulk_d<64, Ts>(a, zmap, mmap, blocks, warps, smem, st);
+        case 128: return launch_bulk_d<128, Ts>(a, zmap, mmap, blocks, warps, smem, st);
+        case 256: return launch_bulk_d<256, Ts>(a, zmap, mmap, blocks, warps, smem, st);
         default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename Ts>
+int bulk_resident_t(int d, int warps, int smem)
+{
+    switch (d) {
+        case 64: return bulk_resident_d<64, Ts>(warps, smem);
+        case 128: return bulk_resident_d<128, Ts>(warps, smem);
+        case 256: return bulk_resident_d<256, Ts>(warps, smem);
+        default: return 0;
     }
 }
 

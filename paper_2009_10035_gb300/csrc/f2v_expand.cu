@@ -1,0 +1,62 @@
+// f2v_expand.cu -- the per-epoch partner list of the staged force kernel.
+//
+// Pair apair[u] + j of vertex u is its j-th neighbour for j < deg(u) and its
+// negative sample k = j - deg(u) otherwise (Alg. 2's two loops, in order).
+// Writing every pair's partner once per epoch lets the force kernel fetch a
+// tile's partners with one coalesced load, instead of a dependent chain
+// (row pointers, then column indices) and a Philox evaluation per sample.
+// Samples follow the same counter layout as everywhere else:
+// w = Philox4x32-10(key, ctr = (u, epoch, k, 0)).x0 mod n.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "f2v_device.cuh"
+#include "f2v_internal.h"
+
+namespace f2v {
+
+namespace {
+
+__global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
+                                       const int32_t *__restrict__ col_idx,
+                                       const int64_t *__restrict__ apair, int32_t n, int32_t s,
+                                       uint32_t epoch, uint32_t key0, uint32_t key1,
+                                       int32_t *__restrict__ partner)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int64_t base = apair[u];
+        const int32_t r0 = row_ptr[u];
+        const int32_t deg = row_ptr[u + 1] - r0;
+        for (int32_t j = lane; j < deg; j += 32) partner[base + j] = col_idx[r0 + j];
+        for (int32_t k = lane; k < s; k += 32) {
+            const uint32_t w = philox_x0((uint32_t)u, epoch, (uint32_t)k, 0u, key0, key1) %
+                               (uint32_t)n;
+            partner[base + deg + k] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
+        }
+        if (deg + s == 0 && lane == 0) partner[base] = kPartnerNone;   // the empty pair
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
+                                   const int64_t *apair, int32_t n, int32_t s, uint32_t epoch,
+                                   uint32_t key0, uint32_t key1, int32_t *partner,
+                                   cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t warps_needed = n;
+    const int blocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)std::max(sms, 1) * 16));
+    expand_partners_kernel<<<blocks, 256, 0, st>>>(row_ptr, col_idx, apair, n, s, epoch, key0,
+                                                   key1, partner);
+    return cudaGetLastError();
+}
+
+}  // namespace f2v

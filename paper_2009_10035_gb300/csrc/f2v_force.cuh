@@ -103,10 +103,34 @@ __device__ __forceinline__ void load_own_row(const ForceArgs<Ts> &a, int u, int 
         load_row<L, VEC, NV, EXACT>(a.zcur + (int64_t)u * a.ld, gl, a.d, x);
 }
 
+// Where a finished vertex's partial sums and row go, for one minibatch.
+struct FinishCtx {
+    int C;                     // pairs per level-0 unit (item or chunk)
+    float *slots;              // combine-tree slots of this minibatch
+    int32_t *unit_cnt;         // combine-tree counters of this minibatch
+    int32_t *row_flag;         // if not null: row_flag[u] = flag_value once row u is written
+    int32_t flag_value;
+};
+
+// Marks row u as written.  The group's lanes stored the row; the warp
+// barrier orders their stores before lane 0's release store of the flag,
+// and release is cumulative, so a reader that acquires the flag sees the
+// whole row.  (A reader that then reads the row through the async proxy
+// issues the proxy fence itself.)
+__device__ __forceinline__ void publish_row(int32_t *flag, int u, int32_t value, unsigned gmask,
+                                            int gl)
+{
+    __syncwarp(gmask);
+    if (gl == 0)
+        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(flag + u), "r"(value)
+                     : "memory");
+}
+
 // z_u <- z_u - eta * g (Eq. 10) into the next buffer (and the master).
 template <int L, int VEC, int NV, bool EXACT, typename Ts>
-__device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, int u, int gl,
-                                          const float *zu, const float *g)
+__device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, const FinishCtx &fc,
+                                          unsigned gmask, int u, int gl, const float *zu,
+                                          const float *g)
 {
     constexpr int E = VEC * NV;
     float z[E];
@@ -122,6 +146,7 @@ __device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, int u, int gl,
                 store_vec<VEC>(a.master + (int64_t)u * a.ld + e0, z + i * VEC);
         }
     }
+    if (fc.row_flag) publish_row(fc.row_flag, u, fc.flag_value, gmask, gl);
 }
 
 // Slot of vertex u (pairs [lb, le) of the minibatch) in level-`lvl` unit j:
@@ -136,24 +161,22 @@ __device__ __forceinline__ int64_t unit_slot(int64_t j, int lb, int64_t unit_pai
 // all of them, else passes the part up the ordered combine tree (g is
 // clobbered).
 template <int L, int VEC, int NV, bool EXACT, typename Ts>
-__device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, unsigned gmask, int gl,
-                                              int unit0, int u, int vbeg, int vend,
-                                              const float *zu, float *g)
+__device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const FinishCtx &fc,
+                                              unsigned gmask, int gl, int unit0, int u, int vbeg,
+                                              int vend, const float *zu, float *g)
 {
     constexpr int E = VEC * NV;
-    int64_t fu = vbeg / a.C, lu = (vend - 1) / a.C;
+    int64_t fu = vbeg / fc.C, lu = (vend - 1) / fc.C;
     if (fu == lu) {
-        write_row<L, VEC, NV, EXACT>(a, u, gl, zu, g);
+        write_row<L, VEC, NV, EXACT>(a, fc, gmask, u, gl, zu, g);
         return;
     }
-    int64_t unit = unit0, unit_pairs = a.C, units = a.units0;
-    float *slot_base = a.slots;
-    int32_t *cnt_base = a.unit_cnt;
+    int64_t unit = unit0, unit_pairs = fc.C, units = a.units0;
+    float *slot_base = fc.slots;
+    int32_t *cnt_base = fc.unit_cnt;
     for (int lvl = 0; lvl + 1 < kMaxLevels; ++lvl) {
         store_row_cg<L, VEC, NV, EXACT>(slot_base + unit_slot(unit, vbeg, unit_pairs) * a.ld,
                                         gl, a.d, g);
-        __threadfence();
-        __syncwarp(gmask);
         const int64_t parent = unit / kFan;
         const int64_t pfu = fu / kFan, plu = lu / kFan;
         const int64_t c0 = max(fu, parent * kFan);
@@ -162,11 +185,19 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, unsigned g
         const int64_t punits = (units + kFan - 1) / kFan;
         int32_t *cnt = top ? &a.counter[u]
                            : &cnt_base[unit_slot(parent, vbeg, unit_pairs * kFan)];
+        // arrive: the group's slot stores, ordered by the warp barrier, are
+        // released by lane 0's acq_rel increment; the last arrival acquires
+        // every sibling's release through the same counter
+        __syncwarp(gmask);
         int prior = 0;
-        if (gl == 0) prior = atomicAdd(cnt, 1);
+        if (gl == 0)
+            asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                         : "=r"(prior)
+                         : "l"(cnt)
+                         : "memory");
         prior = __shfl_sync(gmask, prior, 0, L);
         if (prior != (int)(c1 - c0)) return;      // a sibling completes it
-        __threadfence();
+        __syncwarp(gmask);                         // the other lanes read after the acquire
 #pragma unroll
         for (int e = 0; e < E; ++e) g[e] = 0.f;
         for (int64_t c = c0; c <= c1; c += 4) {    // children in order
@@ -185,7 +216,7 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, unsigned g
         }
         if (gl == 0) *cnt = 0;
         if (top) {
-            write_row<L, VEC, NV, EXACT>(a, u, gl, zu, g);
+            write_row<L, VEC, NV, EXACT>(a, fc, gmask, u, gl, zu, g);
             return;
         }
         slot_base += 2 * units * a.ld;
@@ -214,6 +245,7 @@ __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
     const int gid = (blockIdx.x * warps + (threadIdx.x >> 5)) * G + grp;
     const int ngroups = gridDim.x * warps * G;
     const bool tdist = (a.model == 0);
+    const FinishCtx fc{a.C, a.slots, a.unit_cnt, nullptr, 0};
 
     for (int item = gid; item < a.n_items; item += ngroups) {
         const int q_begin = item * a.C;
@@ -287,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
             const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
             if (w != ucur) {
                 // ---- 4. update: the only place a vertex is finished ------
-                finish_vertex<L, VEC, NV, EXACT>(a, gmask, gl, item, ucur, vbeg, vend, zu, g);
+                finish_vertex<L, VEC, NV, EXACT>(a, fc, gmask, gl, item, ucur, vbeg, vend, zu, g);
                 if (w < 0) break;
                 // next vertex: always ucur + 1, its own row already fetched
                 ucur = w;

@@ -10,10 +10,17 @@ cudaError_t launch_force_fp32(const Shape &sh, const ForceArgs<float> &a, int bl
     return launch_force_any<float>(sh, a, blocks_cap, st);
 }
 
-cudaError_t launch_bulk_fp32(int d, const ForceArgs<float> &a, int blocks, int warps,
-                             int smem_bytes, cudaStream_t st)
+cudaError_t launch_bulk_fp32(int d, const EpochArgs<float> &a, const CUtensorMap &zmap,
+                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
+                             cudaStream_t st)
 {
-    return launch_bulk_t<float>(d, a, blocks, warps, smem_bytes, st);
+    return launch_bulk_t<float>(d, a, zmap, mmap, blocks, warps, smem_bytes, st);
+}
+
+int bulk_resident(int d, bool bf16, int warps, int smem_bytes)
+{
+    return bf16 ? bulk_resident_t<__nv_bfloat16>(d, warps, smem_bytes)
+                : bulk_resident_t<float>(d, warps, smem_bytes);
 }
 
 bool bulk_config(int d, bool bf16, int *warps_per_block, int *smem_bytes)

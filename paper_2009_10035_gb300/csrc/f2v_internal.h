@@ -2,9 +2,12 @@
 // (host driver, force kernels, auxiliary kernels).  Not part of the ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <string>
 
 namespace f2v {
 
@@ -65,6 +68,45 @@ struct ForceArgs {
     int32_t *err;              // device error word (1 = a bounded wait timed out)
 };
 
+// Arguments of one launch: minibatches [k_begin, k_end) of epoch f.epoch.
+// The per-minibatch fields of `f` (P0, Pk, n_items, mb_begin, mb_end, C,
+// item_u0, slots, unit_cnt) are not used; each minibatch's values come from
+// the tables below.
+template <typename Ts>
+struct EpochArgs {
+    ForceArgs<Ts> f;
+    const int32_t *partner;        // partner of every pair of the epoch (expand_partners)
+    const int32_t *items;          // chunk start vertices of every minibatch
+    const int64_t *mb_item_base;   // M + 1: first chunk of each minibatch in `items`
+    const int32_t *mb_C;           // M: pairs per chunk of each minibatch
+    int32_t *row_flag;             // n: epoch + 1 once row v is written this epoch
+    int32_t *mb_done;              // M: chunks finished (zeroed before the launch)
+    float *slots;                  // ring regions of combine-tree slots
+    int32_t *unit_cnt;             // ring regions of combine-tree counters
+    int64_t slot_stride, cnt_stride;
+    int32_t k_begin, k_end, b, ring;
+    // rows of the tensor maps: both Z buffers form one map of 2n rows
+    int32_t zcur_row0, znext_row0;  // first map row of each buffer
+    int32_t own_row0;               // first own row in the own-row map
+};
+
+// TMA map over `rows` rows of d elements (FP32 or BF16) starting at `base`,
+// one box per row, for tile::gather4 loads.  False (and *err) on failure.
+bool make_row_map(CUtensorMap *map, void *base, int64_t rows, int d, bool bf16,
+                  std::string *err);
+
+// Partner codes of the expanded pair list: v >= 0 a neighbour (attractive
+// force), -2 - w a negative sample w (repulsive force), -1 no force (a sample
+// that drew u itself, or the empty pair of a vertex with deg + s = 0).
+constexpr int32_t kPartnerNone = -1;
+
+// Writes the partner code of every pair of epoch `epoch` (pair apair[u] + j
+// of vertex u), one warp per vertex.
+cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
+                                   const int64_t *apair, int32_t n, int32_t s, uint32_t epoch,
+                                   uint32_t key0, uint32_t key1, int32_t *partner,
+                                   cudaStream_t st);
+
 // Kernel shape chosen from d: a group of L lanes owns one force pair at a
 // time; each lane holds NV vectors of VEC consecutive elements of a row.
 struct Shape {
@@ -81,10 +123,16 @@ int items_pairs(const Shape &sh);
 // of d in {64, 128, 256}; it runs `warps` warps per block, one block per SM,
 // each warp walking one chunk.  Returns false if d has no such kernel.
 bool bulk_config(int d, bool bf16, int *warps_per_block, int *smem_bytes);
-cudaError_t launch_bulk_fp32(int d, const ForceArgs<float> &a, int blocks, int warps,
-                             int smem_bytes, cudaStream_t st);
-cudaError_t launch_bulk_bf16(int d, const ForceArgs<__nv_bfloat16> &a, int blocks, int warps,
-                             int smem_bytes, cudaStream_t st);
+// Blocks of that kernel resident per SM (0 if it cannot run).
+int bulk_resident(int d, bool bf16, int warps, int smem_bytes);
+// `zmap` covers both Z buffers (2n rows of the storage type); `mmap` the FP32
+// own rows (the master in the BF16 form, zmap again in the FP32 form).
+cudaError_t launch_bulk_fp32(int d, const EpochArgs<float> &a, const CUtensorMap &zmap,
+                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
+                             cudaStream_t st);
+cudaError_t launch_bulk_bf16(int d, const EpochArgs<__nv_bfloat16> &a, const CUtensorMap &zmap,
+                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
+                             cudaStream_t st);
 
 // Launches the force kernel for one minibatch.  Returns the CUDA error of the
 // launch.  `blocks_cap` bounds the grid (0 = no bound).
