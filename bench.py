@@ -32,7 +32,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2009_10035_gb300/csrc/f2v_bulk.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_force.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_device.cuh",
-                  "paper_2009_10035_gb300/csrc/f2v_force_fp32.cu"]
+                  "paper_2009_10035_gb300/csrc/f2v_force_fp32.cu",
+                  "paper_2009_10035_gb300/csrc/f2v_expand.cu",
+                  "paper_2009_10035_gb300/csrc/f2v_tmap.cu"]
 FALLBACK_HBM_GBS = 6800.0
 
 

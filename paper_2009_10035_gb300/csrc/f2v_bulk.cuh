@@ -614,7 +614,20 @@ cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const
     cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    force_bulk_kernel<D, Ts><<<blocks, warps * 32, smem, st>>>(a, zmap, mmap);
+    // Warps wait on rows and chunks that other blocks produce, so every block
+    // must be resident at once: a cooperative launch guarantees that or fails.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)(warps * 32));
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, force_bulk_kernel<D, Ts>, a, zmap, mmap);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
