@@ -3,6 +3,8 @@
 Each translation unit under csrc/ is compiled for sm_103a only, in parallel,
 then linked with the static CUDA runtime into
 ``paper_2009_10035_gb300/_build/libf2v.so``.  No GPU is needed to build.
+The seeded graph generator (gen/sbm.c, host code) is built separately with
+the C compiler into ``_build/libf2v_gen.so``.
 """
 from __future__ import annotations
 
@@ -80,5 +82,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+GEN_SRC = os.path.join(HERE, "gen", "sbm.c")
+GEN_LIB = os.path.join(BUILD, "libf2v_gen.so")
+
+
+def build_gen(force: bool = False) -> str:
+    """Builds the host-only graph generator (gen/sbm.c) with the C compiler."""
+    if (not force and os.path.exists(GEN_LIB)
+            and os.path.getmtime(GEN_LIB) >= os.path.getmtime(GEN_SRC)):
+        return GEN_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        raise RuntimeError("no C compiler for the graph generator")
+    tmp = GEN_LIB + f".tmp{os.getpid()}"
+    cmd = [cc, "-O2", "-fPIC", "-shared", "-fopenmp", GEN_SRC, "-o", tmp, "-lm"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"graph generator build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_gen(force="--force" in sys.argv))

@@ -68,8 +68,7 @@ __global__ void init_kernel(Ts *z, float *master, int64_t n, int d, uint32_t k0,
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = (uint32_t)(t / d), j = (uint32_t)(t % d);
-        const uint32_t x = philox_x0(i, j, 0xFFFFu, 0u, k0, k1);
-        const float v = (float)(x >> 8) * 5.9604644775390625e-8f - 0.5f;   // 2^-24
+        const float v = z0_value(i, j, k0, k1);
         if constexpr (sizeof(Ts) == 2) {
             z[t] = __float2bfloat16_rn(v);
             master[t] = v;
@@ -322,6 +321,19 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
     }
     return true;
 }
+
+}  // namespace
+
+namespace f2v {
+f2v_status check_csr(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, uint32_t flags)
+{
+    return validate_graph(row_ptr, col_idx, n, flags);
+}
+void set_global_error(const std::string &msg) { g_last_error = msg; }
+std::string global_error() { return g_last_error; }
+}  // namespace f2v
+
+namespace {
 
 double lr_for_epoch(const f2v_ctx *c, int e)
 {

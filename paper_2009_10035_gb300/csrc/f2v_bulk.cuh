@@ -43,7 +43,6 @@
 namespace f2v {
 
 constexpr int kOwnSlots = 8;                 // distinct vertices per tile at most
-constexpr long long kWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -115,12 +114,6 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ int ld_acquire(const int32_t *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 
 // Bounded wait on an mbarrier phase; false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
@@ -133,29 +126,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
-// Bounded wait until *p >= target (acquire); false on time-out.
-__device__ __forceinline__ bool wait_at_least(const int32_t *p, int target)
-{
-    if (ld_acquire(p) >= target) return true;
-    const long long t0 = clock64();
-    while (ld_acquire(p) < target) {
-        if (clock64() - t0 > kWaitCycles) return false;
-        __nanosleep(64);
-    }
-    return true;
-}
-
-// Bounded wait until *p == target (acquire); false on time-out.
-__device__ __forceinline__ bool wait_equal(const int32_t *p, int target)
-{
-    if (ld_acquire(p) == target) return true;
-    const long long t0 = clock64();
-    while (ld_acquire(p) != target) {
-        if (clock64() - t0 > kWaitCycles) return false;
-        __nanosleep(32);
-    }
-    return true;
-}
 
 // Per-warp shared-memory layout.
 template <int D, typename Ts>

@@ -31,6 +31,15 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
     return c0;
 }
 
+// Z0[i][j] = (Philox(ctr=(i, j, 0xFFFF, 0)).x0 >> 8) * 2^-24 - 0.5: a multiple
+// of 2^-24 in [-0.5, 0.5), exact in FP32 (the initial embedding, uniform as
+// the paper's random start).
+__device__ __forceinline__ float z0_value(uint32_t i, uint32_t j, uint32_t k0, uint32_t k1)
+{
+    const uint32_t x = philox_x0(i, j, 0xFFFFu, 0u, k0, k1);
+    return (float)(x >> 8) * 5.9604644775390625e-8f - 0.5f;   // 2^-24
+}
+
 // Row element loads: VEC consecutive elements starting at p, widened to FP32.
 template <int VEC>
 __device__ __forceinline__ void load_vec(const float *p, float *x)
@@ -75,6 +84,24 @@ __device__ __forceinline__ void load_vec_cg(const float *p, float *x)
         x[0] = t.x; x[1] = t.y;
     } else {
         x[0] = __ldcg(p);
+    }
+}
+
+template <int VEC>
+__device__ __forceinline__ void load_vec_cg(const __nv_bfloat16 *p, float *x)
+{
+    if constexpr (VEC == 4) {
+        const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    } else if constexpr (VEC == 2) {
+        const unsigned int t = __ldcg(reinterpret_cast<const unsigned int *>(p));
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
+        x[0] = a.x; x[1] = a.y;
+    } else {
+        const unsigned short t = __ldcg(reinterpret_cast<const unsigned short *>(p));
+        x[0] = __uint_as_float((unsigned int)t << 16);
     }
 }
 
@@ -153,4 +180,39 @@ __device__ __forceinline__ void load_vec_smem(const __nv_bfloat16 *p, float *x)
     }
 }
 
+// Waits between warps of one launch are bounded: about a second at 2 GHz.
+constexpr long long kWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait until *p >= target (acquire); false on time-out.
+__device__ __forceinline__ bool wait_at_least(const int32_t *p, int target)
+{
+    if (ld_acquire(p) >= target) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(p) < target) {
+        if (clock64() - t0 > kWaitCycles) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Bounded wait until *p == target (acquire); false on time-out.
+__device__ __forceinline__ bool wait_equal(const int32_t *p, int target)
+{
+    if (ld_acquire(p) == target) return true;
+    const long long t0 = clock64();
+    while (ld_acquire(p) != target) {
+        if (clock64() - t0 > kWaitCycles) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
 }  // namespace f2v
+

@@ -68,8 +68,8 @@ __device__ __forceinline__ void load_row(const Ts *row, int gl, int d, float *x)
     }
 }
 
-template <int L, int VEC, int NV, bool EXACT>
-__device__ __forceinline__ void load_row_cg(const float *row, int gl, int d, float *x)
+template <int L, int VEC, int NV, bool EXACT, typename Ts>
+__device__ __forceinline__ void load_row_cg(const Ts *row, int gl, int d, float *x)
 {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
@@ -229,12 +229,173 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const Fini
     }
 }
 
+// Partner row v: from the next buffer if an earlier minibatch of this epoch
+// wrote it, else from the current one.  Rows written earlier in the same
+// launch (COHERENT: the batched kernel) are read through L2 only, since L1 is
+// not coherent with other SMs' stores; rows of earlier launches may take the
+// read-only path.
+template <int L, int VEC, int NV, bool EXACT, bool COHERENT, typename Ts>
+__device__ __forceinline__ void load_partner(const ForceArgs<Ts> &a, int v, int gl, float *x)
+{
+    if (v < a.mb_begin) {
+        if constexpr (COHERENT)
+            load_row_cg<L, VEC, NV, EXACT>(a.znext + (int64_t)v * a.ld, gl, a.d, x);
+        else
+            load_row<L, VEC, NV, EXACT>(a.znext + (int64_t)v * a.ld, gl, a.d, x);
+    } else {
+        load_row<L, VEC, NV, EXACT>(a.zcur + (int64_t)v * a.ld, gl, a.d, x);
+    }
+}
+
+// One item (C consecutive pairs of the minibatch) walked by a group of L
+// lanes: lane gl of the group, gmask the group's lanes.
+template <int L, int VEC, int NV, bool EXACT, bool COHERENT, typename Ts>
+__device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishCtx &fc, int item,
+                                           int gl, unsigned gmask)
+{
+    constexpr int E = VEC * NV;
+    constexpr int U = ShapeTraits<L, VEC, NV>::U;
+    const bool tdist = (a.model == 0);
+    const int q_begin = item * a.C;
+    const int q_end = min(q_begin + a.C, a.Pk);
+    int u = __ldg(&a.item_u0[item]);       // vertex holding pair q_begin
+
+    // own rows: the item's first vertex now, the next one ahead of need
+    int ucur = u;
+    float zu[E], zn[E], g[E];
+    load_own_row<L, VEC, NV, EXACT>(a, ucur, gl, zu);
+    if (ucur + 1 < a.mb_end) load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = 0.f;
+    int vbeg = 0, vend = 0;
+
+    // decoded tile (lane gl <-> pair q + gl)
+    int q = q_begin - L;
+    int r = 0, ntile = 0, next_u = u;
+    int pu = u, nb = u, kind = KIND_NONE, pA_hi = 0;
+    for (;;) {
+        if (r == ntile) {
+            // ---- 1. decode the next tile -------------------------------
+            q += L;
+            u = next_u;
+            if (q < q_end) {
+                const int uu = u + gl;
+                int A_hi = INT_MAX;
+                int rp_lo = 0, rp_hi = 0;
+                if (uu < a.n) {
+                    const int64_t ah = __ldg(&a.apair[uu + 1]) - a.P0;
+                    A_hi = ah > INT_MAX ? INT_MAX : (int)ah;
+                    rp_lo = __ldg(&a.row_ptr[uu]);
+                    rp_hi = __ldg(&a.row_ptr[uu + 1]);
+                }
+                const int A_up = __shfl_up_sync(gmask, A_hi, 1, L);
+                const int A_lo = (gl == 0) ? (int)(__ldg(&a.apair[u]) - a.P0) : A_up;
+                const int pos = A_hi - q;             // >= 1: vertex uu ends after q
+                const unsigned bit = (pos < L) ? (1u << pos) : 0u;
+                const unsigned ends = __reduce_or_sync(gmask, bit);
+                const int off = __popc(ends & ((2u << gl) - 1u));
+                pu = u + off;                         // vertex of this lane's pair
+                const int pA_lo = __shfl_sync(gmask, A_lo, off, L);
+                pA_hi = __shfl_sync(gmask, A_hi, off, L);
+                const int prp_lo = __shfl_sync(gmask, rp_lo, off, L);
+                const int prp_hi = __shfl_sync(gmask, rp_hi, off, L);
+                nb = pu;
+                kind = KIND_NONE;
+                if (q + gl < q_end) {
+                    const int j = q + gl - pA_lo;
+                    const int deg = prp_hi - prp_lo;
+                    if (j < deg) {
+                        nb = __ldg(&a.col_idx[prp_lo + j]);
+                        kind = KIND_ATTR;
+                    } else if (j - deg < a.s) {
+                        const uint32_t x0 = philox_x0((uint32_t)pu, a.epoch,
+                                                      (uint32_t)(j - deg), 0u, a.key0, a.key1);
+                        nb = (int)(x0 % (uint32_t)a.n);
+                        kind = (nb == pu) ? KIND_NONE : KIND_REP;
+                    }
+                }
+                if (q == q_begin) {
+                    vbeg = __shfl_sync(gmask, A_lo, 0, L);
+                    vend = __shfl_sync(gmask, A_hi, 0, L);
+                }
+                next_u = u + __popc(__ballot_sync(gmask, pos <= L) & gmask);
+                ntile = min(L, q_end - q);
+                r = 0;
+            }
+        }
+        // vertex of the next pair; -1 once the item is done
+        const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
+        if (w != ucur) {
+            // ---- 4. update: the only place a vertex is finished ------
+            finish_vertex<L, VEC, NV, EXACT>(a, fc, gmask, gl, item, ucur, vbeg, vend, zu, g);
+            if (w < 0) break;
+            // next vertex: always ucur + 1, its own row already fetched
+            ucur = w;
+            vbeg = vend;
+            vend = __shfl_sync(gmask, pA_hi, r, L);
+#pragma unroll
+            for (int e = 0; e < E; ++e) { zu[e] = zn[e]; g[e] = 0.f; }
+            if (ucur + 1 < a.mb_end && vend < q_end)
+                load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
+        }
+        // ---- 2-3. gather and accumulate this vertex's pairs of the tile
+        const int seg_end = min(ntile, vend - q);
+        for (int r0 = r; r0 < seg_end; r0 += U) {
+            float zv[U][E];
+            int kr[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                const int ri = min(r0 + i, L - 1);
+                const int v = __shfl_sync(gmask, nb, ri, L);
+                kr[i] = __shfl_sync(gmask, kind, ri, L);
+                if (r0 + i >= seg_end) kr[i] = KIND_NONE;
+                if (kr[i] != KIND_NONE)
+                    load_partner<L, VEC, NV, EXACT, COHERENT>(a, v, gl, zv[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                if (kr[i] == KIND_NONE) continue;
+                float part = 0.f;
+                if (tdist) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const float df = zu[e] - zv[i][e];
+                        part = fmaf(df, df, part);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
+                }
+#pragma unroll
+                for (int m = L / 2; m >= 1; m >>= 1)
+                    part += __shfl_xor_sync(gmask, part, m, L);
+                if (tdist) {
+                    float coef;
+                    if (kr[i] == KIND_ATTR) {
+                        coef = 2.f / (1.f + part);                 // Eq. 8 / t
+                    } else {
+                        const float q2 = fmaxf(part, kT2Floor);
+                        coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
+                    }
+#pragma unroll
+                    for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
+                } else {
+                    const float coef = (kr[i] == KIND_ATTR)
+                                           ? -1.f / (1.f + expf(part))    // Eq. 5
+                                           : 1.f / (1.f + expf(-part));   // Eq. 6
+#pragma unroll
+                    for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
+                }
+            }
+        }
+        r = seg_end;
+    }
+}
+
 template <int L, int VEC, int NV, bool EXACT, typename Ts>
 __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
 {
     constexpr int G = 32 / L;
-    constexpr int E = VEC * NV;
-    constexpr int U = ShapeTraits<L, VEC, NV>::U;
     static_assert(L >= 1 && L <= 32 && (L & (L - 1)) == 0, "L must be a power of two");
 
     const int lane = threadIdx.x & 31;
@@ -244,147 +405,9 @@ __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
     const int warps = blockDim.x >> 5;
     const int gid = (blockIdx.x * warps + (threadIdx.x >> 5)) * G + grp;
     const int ngroups = gridDim.x * warps * G;
-    const bool tdist = (a.model == 0);
     const FinishCtx fc{a.C, a.slots, a.unit_cnt, nullptr, 0};
-
-    for (int item = gid; item < a.n_items; item += ngroups) {
-        const int q_begin = item * a.C;
-        const int q_end = min(q_begin + a.C, a.Pk);
-        int u = __ldg(&a.item_u0[item]);       // vertex holding pair q_begin
-
-        // own rows: the item's first vertex now, the next one ahead of need
-        int ucur = u;
-        float zu[E], zn[E], g[E];
-        load_own_row<L, VEC, NV, EXACT>(a, ucur, gl, zu);
-        if (ucur + 1 < a.mb_end) load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
-#pragma unroll
-        for (int e = 0; e < E; ++e) g[e] = 0.f;
-        int vbeg = 0, vend = 0;
-
-        // decoded tile (lane gl <-> pair q + gl)
-        int q = q_begin - L;
-        int r = 0, ntile = 0, next_u = u;
-        int pu = u, nb = u, kind = KIND_NONE, pA_hi = 0;
-        for (;;) {
-            if (r == ntile) {
-                // ---- 1. decode the next tile -------------------------------
-                q += L;
-                u = next_u;
-                if (q < q_end) {
-                    const int uu = u + gl;
-                    int A_hi = INT_MAX;
-                    int rp_lo = 0, rp_hi = 0;
-                    if (uu < a.n) {
-                        const int64_t ah = __ldg(&a.apair[uu + 1]) - a.P0;
-                        A_hi = ah > INT_MAX ? INT_MAX : (int)ah;
-                        rp_lo = __ldg(&a.row_ptr[uu]);
-                        rp_hi = __ldg(&a.row_ptr[uu + 1]);
-                    }
-                    const int A_up = __shfl_up_sync(gmask, A_hi, 1, L);
-                    const int A_lo = (gl == 0) ? (int)(__ldg(&a.apair[u]) - a.P0) : A_up;
-                    const int pos = A_hi - q;             // >= 1: vertex uu ends after q
-                    const unsigned bit = (pos < L) ? (1u << pos) : 0u;
-                    const unsigned ends = __reduce_or_sync(gmask, bit);
-                    const int off = __popc(ends & ((2u << gl) - 1u));
-                    pu = u + off;                         // vertex of this lane's pair
-                    const int pA_lo = __shfl_sync(gmask, A_lo, off, L);
-                    pA_hi = __shfl_sync(gmask, A_hi, off, L);
-                    const int prp_lo = __shfl_sync(gmask, rp_lo, off, L);
-                    const int prp_hi = __shfl_sync(gmask, rp_hi, off, L);
-                    nb = pu;
-                    kind = KIND_NONE;
-                    if (q + gl < q_end) {
-                        const int j = q + gl - pA_lo;
-                        const int deg = prp_hi - prp_lo;
-                        if (j < deg) {
-                            nb = __ldg(&a.col_idx[prp_lo + j]);
-                            kind = KIND_ATTR;
-                        } else if (j - deg < a.s) {
-                            const uint32_t x0 = philox_x0((uint32_t)pu, a.epoch,
-                                                          (uint32_t)(j - deg), 0u, a.key0, a.key1);
-                            nb = (int)(x0 % (uint32_t)a.n);
-                            kind = (nb == pu) ? KIND_NONE : KIND_REP;
-                        }
-                    }
-                    if (q == q_begin) {
-                        vbeg = __shfl_sync(gmask, A_lo, 0, L);
-                        vend = __shfl_sync(gmask, A_hi, 0, L);
-                    }
-                    next_u = u + __popc(__ballot_sync(gmask, pos <= L) & gmask);
-                    ntile = min(L, q_end - q);
-                    r = 0;
-                }
-            }
-            // vertex of the next pair; -1 once the item is done
-            const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
-            if (w != ucur) {
-                // ---- 4. update: the only place a vertex is finished ------
-                finish_vertex<L, VEC, NV, EXACT>(a, fc, gmask, gl, item, ucur, vbeg, vend, zu, g);
-                if (w < 0) break;
-                // next vertex: always ucur + 1, its own row already fetched
-                ucur = w;
-                vbeg = vend;
-                vend = __shfl_sync(gmask, pA_hi, r, L);
-#pragma unroll
-                for (int e = 0; e < E; ++e) { zu[e] = zn[e]; g[e] = 0.f; }
-                if (ucur + 1 < a.mb_end && vend < q_end)
-                    load_own_row<L, VEC, NV, EXACT>(a, ucur + 1, gl, zn);
-            }
-            // ---- 2-3. gather and accumulate this vertex's pairs of the tile
-            const int seg_end = min(ntile, vend - q);
-            for (int r0 = r; r0 < seg_end; r0 += U) {
-                float zv[U][E];
-                int kr[U];
-#pragma unroll
-                for (int i = 0; i < U; ++i) {
-                    const int ri = min(r0 + i, L - 1);
-                    const int v = __shfl_sync(gmask, nb, ri, L);
-                    kr[i] = __shfl_sync(gmask, kind, ri, L);
-                    if (r0 + i >= seg_end) kr[i] = KIND_NONE;
-                    if (kr[i] != KIND_NONE) {
-                        const Ts *src = (v < a.mb_begin) ? a.znext : a.zcur;
-                        load_row<L, VEC, NV, EXACT>(src + (int64_t)v * a.ld, gl, a.d, zv[i]);
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < U; ++i) {
-                    if (kr[i] == KIND_NONE) continue;
-                    float part = 0.f;
-                    if (tdist) {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            const float df = zu[e] - zv[i][e];
-                            part = fmaf(df, df, part);
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
-                    }
-#pragma unroll
-                    for (int m = L / 2; m >= 1; m >>= 1)
-                        part += __shfl_xor_sync(gmask, part, m, L);
-                    if (tdist) {
-                        float coef;
-                        if (kr[i] == KIND_ATTR) {
-                            coef = 2.f / (1.f + part);                 // Eq. 8 / t
-                        } else {
-                            const float q2 = fmaxf(part, kT2Floor);
-                            coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
-                        }
-#pragma unroll
-                        for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
-                    } else {
-                        const float coef = (kr[i] == KIND_ATTR)
-                                               ? -1.f / (1.f + expf(part))    // Eq. 5
-                                               : 1.f / (1.f + expf(-part));   // Eq. 6
-#pragma unroll
-                        for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
-                    }
-                }
-            }
-            r = seg_end;
-        }
-    }
+    for (int item = gid; item < a.n_items; item += ngroups)
+        force_item<L, VEC, NV, EXACT, false>(a, fc, item, gl, gmask);
 }
 
 template <int L, int VEC, int NV, bool EXACT, typename Ts>

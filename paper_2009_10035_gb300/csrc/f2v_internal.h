@@ -9,6 +9,8 @@
 
 #include <string>
 
+#include "f2v.h"
+
 namespace f2v {
 
 // Arguments of one launch of the fused force+update kernel: the work of one
@@ -140,5 +142,106 @@ cudaError_t launch_force_fp32(const Shape &sh, const ForceArgs<float> &a, int bl
                               cudaStream_t st);
 cudaError_t launch_force_bf16(const Shape &sh, const ForceArgs<__nv_bfloat16> &a,
                               int blocks_cap, cudaStream_t st);
+
+// Host-side checks shared by the entry points (f2v_api.cu): the CSR rules of
+// f2v_create (message in the thread's global error), and that error string.
+f2v_status check_csr(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, uint32_t flags);
+void set_global_error(const std::string &msg);
+std::string global_error();
+
+// ---- batched form (f2v_batch.cuh, f2v_batch.cu) -----------------------------
+//
+// A batch is a set of independent graphs stepped one epoch at a time by one
+// persistent launch per row shape.  A launch's work is a queue of warp units;
+// a unit is 32 / L consecutive items (one per lane group) of one minibatch
+// record.
+
+// Row shapes of the batched kernel: (L lanes per row, VEC elements per lane),
+// L * VEC = d, NV = 1.  kBatchShapes lists them; the code of a shape is its
+// index.
+struct BatchShape {
+    int d, L, VEC;
+};
+constexpr int kNumBatchShapes = 12;
+constexpr BatchShape kBatchShapes[kNumBatchShapes] = {
+    {2, 1, 2},   {4, 1, 4},   {4, 2, 2},   {8, 2, 4},   {8, 4, 2},   {16, 4, 4},
+    {16, 8, 2},  {32, 8, 4},  {32, 16, 2}, {64, 16, 4}, {64, 32, 2}, {128, 32, 4},
+};
+
+// One graph of a batch (device table, rebuilt with the work tables).
+struct BatchGraph {
+    const int32_t *row_ptr;    // n + 1, local offsets into col_idx
+    const int32_t *col_idx;    // local vertex ids
+    const int64_t *apair;      // n + 1 pair prefix (as ForceArgs::apair)
+    void *z[2];                // storage rows of the two buffers (n x d)
+    float *master;             // BF16 form: FP32 master rows; else nullptr
+    int32_t *counter;          // n final-arrival counters of the combine tree
+    int32_t n, d, shape;       // shape: index into kBatchShapes
+    uint32_t key0, key1;       // Philox key = (seed lo, seed hi)
+    float lr;                  // eta schedule of this graph
+    int32_t schedule, total_epochs;
+};
+
+// Epoch state of one graph, advanced on the device after each epoch.
+struct BatchState {
+    uint32_t epoch;            // epoch counter e (samples, eta)
+    int32_t cur;               // buffer holding Z as of the epoch's start
+    float eta;                 // eta_e
+    int32_t pad;
+};
+
+// One minibatch (graph g, minibatch k) of an epoch.
+struct BatchRec {
+    int64_t P0;                // local index of its first pair
+    int64_t slot_off;          // its combine-tree slots (floats into the pool)
+    int64_t cnt_off;           // its combine-tree counters (ints into the pool)
+    int32_t g, mb_begin, mb_end;
+    int32_t Pk, C, n_items;
+    int32_t item_off;          // its items' start vertices in BatchArgs::item_u0
+    int32_t n_wunits;          // warp units of this minibatch
+    int32_t prev;              // record of minibatch k - 1 of graph g, or -1
+    int32_t pad;
+};
+
+struct BatchUnit {
+    int32_t rec, item0;        // items item0 .. item0 + 32/L - 1 of record rec
+};
+
+template <typename Ts>
+struct BatchArgs {
+    const BatchGraph *graphs;
+    BatchState *state;
+    const BatchRec *recs;
+    const BatchUnit *units;    // this launch's queue (one shape), in order
+    const int32_t *item_u0;
+    float *slots;
+    int32_t *unit_cnt;
+    int32_t *done;             // per record: warp units finished (zero at launch)
+    int32_t *next_unit;        // queue head (zero at launch)
+    int32_t n_units, n_graphs;
+    int32_t s, model;
+    int32_t *err;              // 2 = a minibatch barrier wait timed out
+};
+
+constexpr int kBatchBlock = 256;
+
+// Host: eta of epoch e (the same arithmetic as the single-graph context).
+inline double batch_eta(float lr, int schedule, int total_epochs, int e)
+{
+    if (schedule == 1 && total_epochs > 0)
+        return (double)lr * (1.0 - (double)e / (double)total_epochs);
+    return (double)lr;
+}
+
+// Launches the batched kernel of one shape over the queue in `a`.
+cudaError_t launch_batch_fp32(int shape, const BatchArgs<float> &a, int blocks, cudaStream_t st);
+cudaError_t launch_batch_bf16(int shape, const BatchArgs<__nv_bfloat16> &a, int blocks,
+                              cudaStream_t st);
+// Blocks of the batched kernel of a shape resident per SM.
+int batch_resident(int shape, bool bf16);
+cudaError_t launch_batch_advance(const BatchGraph *graphs, BatchState *state, int n_graphs,
+                                 cudaStream_t st);
+cudaError_t launch_batch_init(const BatchGraph *graphs, int n_graphs, bool bf16, int64_t max_elems,
+                              cudaStream_t st);
 
 }  // namespace f2v

@@ -28,7 +28,8 @@ _STATUS = {0: "F2V_OK", 1: "F2V_EINVAL", 2: "F2V_ENOMEM", 3: "F2V_ECUDA",
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libf2v.so")
-HEADER = os.path.join(os.path.dirname(_HERE), "include", "f2v.h")
+INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+HEADER = os.path.join(INCLUDE, "f2v.h")
 
 _lock = threading.Lock()
 _lib = None
@@ -41,11 +42,16 @@ class F2VError(RuntimeError):
 
 
 def header_functions() -> list[str]:
-    """Names of the functions include/f2v.h declares."""
-    with open(HEADER) as f:
-        text = f.read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(f2v_[a-z0-9_]+)\s*\(", text)))
+    """Names of the functions the headers under include/ declare."""
+    names = set()
+    for fn in sorted(os.listdir(INCLUDE)):
+        if not fn.endswith(".h"):
+            continue
+        with open(os.path.join(INCLUDE, fn)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names.update(re.findall(r"\b(f2v_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -91,6 +97,30 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_noalloc_last_error": ([], ctypes.c_char_p),
             "f2v_last_error": ([vp], ctypes.c_char_p),
             "f2v_last_error_global": ([], ctypes.c_char_p),
+            # batched form (include/f2v_batch.h)
+            "f2v_batch_create": ([i32, vp, vp, vp, vp, vp, st, i32, f32, i32, st, vp, pp], st),
+            "f2v_batch_destroy": ([vp], None),
+            "f2v_batch_epoch": ([vp], st),
+            "f2v_batch_train": ([vp, i32], st),
+            "f2v_batch_synchronize": ([vp], st),
+            "f2v_batch_run_minibatches": ([vp, i32], st),
+            "f2v_batch_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "f2v_batch_set_lr": ([vp, f32], st),
+            "f2v_batch_set_schedule": ([vp, st, i32], st),
+            "f2v_batch_get_epoch": ([vp, ctypes.POINTER(i32)], st),
+            "f2v_batch_get_embedding": ([vp, i32, vp, sz], st),
+            "f2v_batch_get_embeddings": ([vp, vp, sz], st),
+            "f2v_batch_set_embedding": ([vp, i32, vp, sz], st),
+            "f2v_batch_set_tiling": ([vp, vp], st),
+            "f2v_batch_get_tiling": ([vp, i32, vp], st),
+            "f2v_batch_autotune": ([vp, i32, vp, i32, ctypes.POINTER(i32)], st),
+            "f2v_batch_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+            "f2v_batch_bytes_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+            "f2v_batch_device_bytes": ([vp, ctypes.POINTER(sz)], st),
+            "f2v_batch_num_graphs": ([vp, ctypes.POINTER(i32)], st),
+            "f2v_batch_launch_count": ([vp, ctypes.POINTER(i64)], st),
+            "f2v_batch_stream": ([vp, pp], st),
+            "f2v_batch_last_error": ([vp], ctypes.c_char_p),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -261,3 +291,189 @@ class Context:
 def create(graph, d: int, **kw) -> Context:
     """Context for a ``graphs.Graph``."""
     return Context(graph.row_ptr, graph.col_idx, graph.n, d, **kw)
+
+
+class Tiling(ctypes.Structure):
+    """f2v_tiling: lanes per row (L) and pairs per item (C) for row size d."""
+    _fields_ = [("d", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32),
+                ("item_pairs", ctypes.c_int32)]
+
+    def as_tuple(self) -> tuple[int, int, int]:
+        return (self.d, self.lanes_per_row, self.item_pairs)
+
+
+class Batch:
+    """Many graphs trained together (include/f2v_batch.h): one persistent
+    kernel launch per row shape and epoch, replayed from a CUDA graph."""
+
+    def __init__(self, n, d, seed, row_ptr, col_idx, model: int = TDIST, s: int = 5,
+                 lr: float = 0.02, minibatch: int = 128, precision: int = FP32, stream=None):
+        self._lib = load_library()
+        self.n = np.ascontiguousarray(n, np.int32)
+        self.d = np.ascontiguousarray(d, np.int32)
+        sd = np.ascontiguousarray(np.asarray(seed).astype(np.uint64))
+        rp = np.ascontiguousarray(row_ptr, np.int32)
+        ci = np.ascontiguousarray(col_idx, np.int32)
+        if ci.size == 0:
+            ci = np.zeros(1, np.int32)
+        G = int(self.n.size)
+        if self.d.size != G or sd.size != G:
+            raise ValueError("n, d and seed must have one entry per graph")
+        if rp.size != int(self.n.astype(np.int64).sum()) + G:
+            raise ValueError("row_ptr must hold n[g] + 1 entries per graph")
+        self.s, self.model, self.precision = int(s), int(model), int(precision)
+        h = ctypes.c_void_p()
+        rc = self._lib.f2v_batch_create(G, _ptr(self.n), _ptr(self.d), _ptr(sd), _ptr(rp),
+                                        _ptr(ci), int(model), int(s), float(lr), int(minibatch),
+                                        int(precision), _stream_handle(stream), ctypes.byref(h))
+        if rc != OK:
+            raise F2VError(rc, self._lib.f2v_last_error_global().decode())
+        self._h = h
+        self.z_off = np.zeros(G + 1, np.int64)
+        self.z_off[1:] = np.cumsum(self.n.astype(np.int64) * self.d)
+
+    @classmethod
+    def from_graphs(cls, batch, **kw) -> "Batch":
+        """Batch over a ``graphs.GraphBatch`` (its n, d, seeds and CSRs)."""
+        return cls(batch.n, batch.d, batch.seed, batch.row_ptr, batch.col_idx, **kw)
+
+    def _check(self, rc: int):
+        if rc != OK:
+            msg = self._lib.f2v_batch_last_error(self._h).decode() if self._h else ""
+            raise F2VError(rc, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.f2v_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def num_graphs(self) -> int:
+        return int(self.n.size)
+
+    def epoch(self):
+        self._check(self._lib.f2v_batch_epoch(self._h))
+
+    def train(self, epochs: int):
+        self._check(self._lib.f2v_batch_train(self._h, int(epochs)))
+
+    def run_minibatches(self, count: int):
+        self._check(self._lib.f2v_batch_run_minibatches(self._h, int(count)))
+
+    @property
+    def progress(self) -> tuple[int, int]:
+        e = ctypes.c_int32()
+        k = ctypes.c_int32()
+        self._check(self._lib.f2v_batch_get_progress(self._h, ctypes.byref(e), ctypes.byref(k)))
+        return e.value, k.value
+
+    def synchronize(self):
+        self._check(self._lib.f2v_batch_synchronize(self._h))
+
+    def set_lr(self, lr: float):
+        self._check(self._lib.f2v_batch_set_lr(self._h, float(lr)))
+
+    def set_schedule(self, schedule: int, total_epochs: int):
+        self._check(self._lib.f2v_batch_set_schedule(self._h, int(schedule), int(total_epochs)))
+
+    @property
+    def epoch_counter(self) -> int:
+        e = ctypes.c_int32()
+        self._check(self._lib.f2v_batch_get_epoch(self._h, ctypes.byref(e)))
+        return e.value
+
+    def embedding(self, g: int) -> np.ndarray:
+        out = np.empty((int(self.n[g]), int(self.d[g])), np.float32)
+        self._check(self._lib.f2v_batch_get_embedding(self._h, int(g), _ptr(out), out.size))
+        return out
+
+    def embeddings_into_host(self, out: np.ndarray):
+        """All graphs' Z, concatenated in graph order (row-major per graph)."""
+        assert out.dtype == np.float32 and out.flags.c_contiguous
+        self._check(self._lib.f2v_batch_get_embeddings(self._h, _ptr(out), out.size))
+
+    def set_embedding(self, g: int, z):
+        z = np.ascontiguousarray(z, np.float32)
+        self._check(self._lib.f2v_batch_set_embedding(self._h, int(g), _ptr(z), z.size))
+
+    def set_tiling(self, d: int, lanes_per_row: int, item_pairs: int):
+        t = Tiling(int(d), int(lanes_per_row), int(item_pairs))
+        self._check(self._lib.f2v_batch_set_tiling(self._h, ctypes.byref(t)))
+
+    def tiling(self, d: int) -> tuple[int, int, int]:
+        t = Tiling()
+        self._check(self._lib.f2v_batch_get_tiling(self._h, int(d), ctypes.byref(t)))
+        return t.as_tuple()
+
+    def autotune(self, epochs_per_candidate: int = 1, cache: str | None = None,
+                 key: str | None = None) -> list[tuple[int, int, int]]:
+        """Times candidate tilings on this batch and applies the fastest
+        (embeddings and epoch counter are restored).  With `cache` (a JSON
+        file) and `key`, a tiling found earlier under `key` is applied
+        instead, and a new one is stored there."""
+        import json
+        if cache and key and os.path.exists(cache):
+            with open(cache) as f:
+                known = json.load(f)
+            if key in known:
+                for d, L, C in known[key]:
+                    self.set_tiling(d, L, C)
+                return [tuple(x) for x in known[key]]
+        arr = (Tiling * 8)()
+        cnt = ctypes.c_int32()
+        self._check(self._lib.f2v_batch_autotune(self._h, int(epochs_per_candidate), arr, 8,
+                                                 ctypes.byref(cnt)))
+        chosen = [arr[i].as_tuple() for i in range(cnt.value)]
+        if cache and key:
+            known = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f)
+            known[key] = [list(t) for t in chosen]
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return chosen
+
+    @property
+    def pairs_per_epoch(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.f2v_batch_pairs_per_epoch(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def bytes_per_epoch(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.f2v_batch_bytes_per_epoch(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        self._check(self._lib.f2v_batch_device_bytes(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def launch_count(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.f2v_batch_launch_count(self._h, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def stream(self) -> int:
+        v = ctypes.c_void_p()
+        self._check(self._lib.f2v_batch_stream(self._h, ctypes.byref(v)))
+        return v.value or 0

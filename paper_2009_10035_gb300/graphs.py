@@ -16,6 +16,9 @@ Generators (numpy ``PCG64``, identical output on every platform for a seed):
                       for graphs with community structure.
   * ``holdout``       removes a fraction of undirected edges (both directions)
                       for link prediction and draws as many non-edge pairs.
+  * ``sbm_batch``     many SBM graphs of log-uniform size and random block
+                      counts at once (the batched and served workloads), drawn
+                      by the C helper gen/sbm.c (xoshiro256** per graph).
 
 All graphs are returned as symmetric CSR with int32 ``row_ptr`` (n+1) and
 ``col_idx`` (nnz), each row sorted, no self-loops, no duplicates; the
@@ -252,3 +255,91 @@ def config2_graph(seed: int = 1, scale: int = 20, frac: float = 0.05) -> Graph:
     """R-MAT scale-20 (16 * 2^20 directed edges, a=.57, b=c=.19), symmetrised,
     with `frac` of the undirected edges held out."""
     return holdout(rmat(scale, 16, seed=seed), frac=frac, seed=seed + 1000)
+
+
+@dataclass
+class GraphBatch:
+    """Many graphs in the concatenated layout of include/f2v_batch.h."""
+    n: np.ndarray          # int32 [G]
+    d: np.ndarray          # int32 [G] row size of each graph's embedding
+    blocks: np.ndarray     # int32 [G]
+    seed: np.ndarray       # uint64 [G] embedding seeds
+    row_ptr: np.ndarray    # int32, graph g's n[g]+1 entries after graph g-1's
+    col_idx: np.ndarray    # int32, local ids
+    row_off: np.ndarray = field(default=None)   # int64 [G+1]
+    col_off: np.ndarray = field(default=None)   # int64 [G+1]
+    name: str = ""
+
+    @property
+    def num_graphs(self) -> int:
+        return int(self.n.size)
+
+    def graph(self, g: int) -> Graph:
+        rp = self.row_ptr[self.row_off[g]:self.row_off[g + 1]]
+        ci = self.col_idx[self.col_off[g]:self.col_off[g + 1]]
+        return Graph(int(self.n[g]), rp, ci, name=f"{self.name}[{g}]")
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.size)
+
+
+_gen_lib = None
+
+
+def _gen():
+    global _gen_lib
+    if _gen_lib is None:
+        import ctypes
+        from . import build
+        lib = ctypes.CDLL(build.build_gen())
+        lib.f2v_sbm_begin.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
+                                      ctypes.c_void_p]
+        lib.f2v_sbm_begin.restype = ctypes.c_void_p
+        lib.f2v_sbm_finish.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.f2v_sbm_finish.restype = None
+        _gen_lib = lib
+    return _gen_lib
+
+
+def sbm_graphs(n, blocks, p_in: float, p_out: float, seed: int = 1):
+    """Symmetric CSRs of SBM graphs with the given sizes and block counts
+    (concatenated layout); returns (row_ptr, col_idx, row_off, col_off)."""
+    n = np.ascontiguousarray(n, np.int32)
+    blocks = np.ascontiguousarray(blocks, np.int32)
+    G = int(n.size)
+    nnz = np.zeros(G, np.int64)
+    lib = _gen()
+    h = lib.f2v_sbm_begin(G, n.ctypes.data, blocks.ctypes.data, float(p_in), float(p_out),
+                          int(seed) & 0xFFFFFFFFFFFFFFFF, nnz.ctypes.data)
+    if not h:
+        raise MemoryError("graph generator out of memory")
+    row_off = np.zeros(G + 1, np.int64)
+    row_off[1:] = np.cumsum(n.astype(np.int64) + 1)
+    col_off = np.zeros(G + 1, np.int64)
+    col_off[1:] = np.cumsum(nnz)
+    if col_off[-1] >= 2**31 * 64:
+        raise ValueError("batch too large")
+    row_ptr = np.empty(int(row_off[-1]), np.int32)
+    col_idx = np.empty(max(int(col_off[-1]), 1), np.int32)
+    lib.f2v_sbm_finish(h, row_ptr.ctypes.data, col_idx.ctypes.data)
+    return row_ptr, col_idx[:int(col_off[-1])], row_off, col_off
+
+
+def sbm_batch(num_graphs: int, seed: int = 1, n_range=(50, 20000), block_range=(2, 16),
+              p_in: float = 0.05, p_out: float = 0.002, dims=(2, 16, 64)) -> GraphBatch:
+    """The batched workload: `num_graphs` SBM graphs, n log-uniform in
+    n_range, block counts uniform in block_range (inclusive), row sizes
+    taken round-robin from `dims`, embedding seeds drawn per graph."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    n = np.exp(rng.uniform(lo, hi, num_graphs)).astype(np.int32)
+    n = np.clip(n, n_range[0], n_range[1]).astype(np.int32)
+    blocks = rng.integers(block_range[0], block_range[1] + 1, num_graphs).astype(np.int32)
+    blocks = np.minimum(blocks, n).astype(np.int32)
+    d = np.asarray([dims[i % len(dims)] for i in range(num_graphs)], np.int32)
+    seeds = rng.integers(1, 2**63, num_graphs, dtype=np.int64).astype(np.uint64)
+    rp, ci, roff, coff = sbm_graphs(n, blocks, p_in, p_out, seed=seed)
+    return GraphBatch(n, d, blocks, seeds, rp, ci, roff, coff,
+                      name=f"sbm-batch-G{num_graphs}-seed{seed}")
