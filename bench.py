@@ -56,8 +56,11 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["single", "batched"], default="single",
-                    help="single: one R-MAT graph (the headline); batched: 4,096 SBM graphs")
+    ap.add_argument("--workload", choices=["single", "batched", "served"], default="single",
+                    help="single: one R-MAT graph (the headline); batched: 4,096 SBM graphs; "
+                         "served: Poisson job arrivals to the job server")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
+    ap.add_argument("--window", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched: default tiling, no autotune")
     return ap.parse_args()
@@ -520,17 +523,116 @@ def run_batched(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# served workload: Poisson arrivals of R-MAT jobs to the job server
+# --------------------------------------------------------------------------
+
+SERVE_BUDGET = 120 << 30
+SERVE_EPOCHS = 10
+SERVE_MINIBATCH = 4096
+
+
+def serve_pool(seed=11):
+    """One R-MAT graph per scale 10..21 (n = 2^10 .. 2^21, so that n is
+    log-uniform over [1e3, 2e6] when the scale is drawn uniformly), average
+    degree drawn from U[8, 32] (edge factor = degree / 2 before symmetrising)."""
+    from paper_2009_10035_gb300 import graphs
+    rng = np.random.default_rng(seed)
+    pool = {}
+    for sc in range(10, 22):
+        ef = max(4, int(round(rng.uniform(8, 32) / 2)))
+        pool[sc] = graphs.rmat(sc, ef, seed=int(rng.integers(1, 1 << 30)))
+    return pool
+
+
+def run_served(args, world, rank, local):
+    import torch
+    from paper_2009_10035_gb300 import f2v
+
+    torch.cuda.set_device(local)
+    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    t_pool = time.perf_counter()
+    pool = serve_pool()
+    pinned = {sc: (torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col_idx).pin_memory())
+              for sc, g in pool.items()}
+    t_pool = time.perf_counter() - t_pool
+    out = torch.empty(max(g.n for g in pool.values()) * 128, dtype=torch.float32).pin_memory()
+    out_np = out.numpy()
+    dims = (2, 32, 128)
+    rng = np.random.default_rng(1234 + rank)
+
+    def submit(srv, sc, d, seed):
+        rp, ci = pinned[sc]
+        g = pool[sc]
+        return srv.submit(rp.numpy(), ci.numpy(), g.n, d=d, model=model, s=5, lr=0.02,
+                          minibatch=SERVE_MINIBATCH, seed=seed, epochs=SERVE_EPOCHS,
+                          precision=f2v.BF16, out=out_np)
+
+    srv = f2v.Server(budget_bytes=SERVE_BUDGET)
+    # warm-up: one job of each row size at the largest scale builds the groups
+    for d in dims:
+        submit(srv, 12, d, 1)
+    srv.wait_all()
+    base = srv.stats()
+    # arrivals: Poisson process at args.rate for args.window seconds
+    gaps = rng.exponential(1.0 / args.rate, int(args.rate * args.window * 1.5) + 10)
+    times = np.cumsum(gaps)
+    times = times[times < args.window]
+    scales = rng.integers(10, 22, times.size)
+    dsel = rng.integers(0, len(dims), times.size)
+    ids = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i, t in enumerate(times):
+            now = time.perf_counter() - t0
+            if t > now:
+                time.sleep(t - now)
+            ids.append(submit(srv, int(scales[i]), dims[int(dsel[i])], 1000 + i))
+        t_end = time.perf_counter() - t0
+        st = srv.stats()
+    infos = [srv.info(j) for j in ids]
+    done = [i for i in infos if i.state == f2v.JOB_DONE]
+    lat = np.array([i.finish_s - i.submit_s for i in done]) if done else np.zeros(0)
+    pairs = st.pairs_done - base.pairs_done
+    window = max(t_end, 1e-9)
+    srv.close()        # jobs still running or queued are stopped
+    pct = (lambda q: float(np.percentile(lat, q)) if lat.size else None)
+    offered = sum((pool[int(scales[i])].nnz + pool[int(scales[i])].n * 5) * SERVE_EPOCHS
+                  for i in range(times.size))
+    if rank == 0:
+        line = {
+            "metric": "force-pair updates/s (served)", "value": pairs / window,
+            "unit": "pairs/s", "n_gpus": world, "steps": int(st.steps - base.steps),
+            "warmup": 3, "ms_per_step": 1e3 * window / max(st.steps - base.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": f"force2vec-served poisson{args.rate:g}/s window{args.window:g}s",
+                       "jobs": "R-MAT n = 2^10..2^21 (scale uniform), avg degree U[8,32], "
+                               "d in {2, 32, 128} BF16 storage, s 5, 10 epochs, minibatch 4096",
+                       "budget_gb": SERVE_BUDGET / 2**30, "pool_build_s": t_pool},
+            "latency_s": {"p50": pct(50), "p99": pct(99), "mean": float(lat.mean()) if lat.size else None,
+                          "completed": len(done), "submitted": len(ids),
+                          "running_at_end": int(st.running), "queued_at_end": int(st.queued)},
+            "offered_pairs_per_s": offered / args.window,
+            "peak_device_gb": st.peak_bytes / 2**30,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     from paper_2009_10035_gb300 import graphs
-    if args.workload == "batched":
+    if args.workload in ("batched", "served"):
         if args.impl == "reference":
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable":
                                   "the oracle arm is timed on the single-graph workload"}))
-        else:
+        elif args.workload == "batched":
             run_batched(args, world, rank, local)
+        else:
+            run_served(args, world, rank, local)
     else:
         g = graphs.config2_graph(scale=args.scale)
         if args.impl == "reference":

@@ -76,6 +76,33 @@ __global__ void batch_round_kernel(__nv_bfloat16 *z, const float *master, int64_
         z[t] = __float2bfloat16_rn(master[t]);
 }
 
+// Expands the records of an epoch into the start vertex of every item (the
+// vertex holding pair P0 + i C, found by binary search over the minibatch's
+// pair prefix) and the warp units of every record, at the offsets the host
+// assigned.
+__global__ void batch_expand_kernel(const BatchGraph *graphs, const BatchRec *recs, int R,
+                                    int32_t *item_u0, BatchUnit *units)
+{
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        const BatchRec rec = recs[r];
+        const int64_t *ap = graphs[rec.g].apair;
+        for (int i = threadIdx.x; i < rec.n_items; i += blockDim.x) {
+            const int64_t q = rec.P0 + (int64_t)i * rec.C;
+            int lo = rec.mb_begin, hi = rec.mb_end - 1;   // largest u with apair[u] <= q
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ap[mid] <= q)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            item_u0[rec.item_off + i] = lo;
+        }
+        for (int w = threadIdx.x; w < rec.n_wunits; w += blockDim.x)
+            units[rec.unit_off + w] = BatchUnit{r, w * rec.gsize};
+    }
+}
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 int grid_for(int64_t elems)
@@ -191,9 +218,20 @@ size_t BatchEngine::graph_bytes(int64_t n, int d, int64_t nnz) const
     return b;
 }
 
+size_t BatchEngine::table_bytes(int64_t pairs, int64_t n, int d) const
+{
+    // items (4 B) and up to two slot rows per item, records per minibatch,
+    // warp units: bounded with the smallest item size in use
+    int Cmin = 8192;
+    for (const BatchTile &t : tiles_) Cmin = std::min(Cmin, std::max(t.C, 32));
+    const int64_t items = pairs / Cmin + (n + b_ - 1) / b_ + 1;
+    return (size_t)items * (4 + 8 + 2 * 2 * (size_t)d * 4 + 16) +
+           (size_t)((n + b_ - 1) / b_ + 1) * (sizeof(BatchRec) + 4);
+}
+
 int BatchEngine::add_graph(const int32_t *row_ptr, const int32_t *col_idx, int n, int d,
                            uint64_t seed, float lr, int schedule, int total_epochs,
-                           f2v_status *st)
+                           f2v_status *st, bool validated)
 {
     *st = F2V_OK;
     if (failed_) {
@@ -216,10 +254,12 @@ int BatchEngine::add_graph(const int32_t *row_ptr, const int32_t *col_idx, int n
         *st = fail(F2V_EINVAL, "linear schedule needs total_epochs >= 1");
         return -1;
     }
-    f2v_status vs = check_csr(row_ptr, col_idx, n, 0);
-    if (vs != F2V_OK) {
-        *st = fail(vs, "%s", global_error().c_str());
-        return -1;
+    if (!validated) {
+        f2v_status vs = check_csr(row_ptr, col_idx, n, 0);
+        if (vs != F2V_OK) {
+            *st = fail(vs, "%s", global_error().c_str());
+            return -1;
+        }
     }
     Graph g;
     g.n = n;
@@ -428,9 +468,8 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
     std::vector<BatchGraph> hg((size_t)P);
     std::vector<BatchState> hs((size_t)P);
     std::vector<BatchRec> recs;
-    std::vector<int32_t> items;
     std::vector<double> keys;
-    int64_t slot_total = 0, cnt_total = 0;
+    int64_t slot_total = 0, cnt_total = 0, item_total = 0;
     try {
         for (int p = 0; p < P; ++p) {
             Graph &g = graphs_[(size_t)pos_[(size_t)p]];
@@ -440,8 +479,7 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
             hs[(size_t)p] = BatchState{(uint32_t)g.epoch, g.cur,
                                        (float)batch_eta(g.lr, g.schedule, g.total_epochs, g.epoch),
                                        0};
-            const int L = kBatchShapes[t.shape].L;
-            const int G = 32 / L;
+            const int G = 32 / kBatchShapes[t.shape].L;
             const int C = t.C;
             const int M = (g.n + b_ - 1) / b_;
             for (int k = k_lo; k < std::min(M, k_hi); ++k) {
@@ -455,15 +493,11 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
                 r.Pk = (int32_t)(P1 - P0);
                 r.C = C;
                 r.n_items = (int32_t)((P1 - P0 + C - 1) / C);
-                r.item_off = (int32_t)items.size();
+                r.item_off = (int32_t)std::min<int64_t>(item_total, INT32_MAX);
+                item_total += r.n_items;
                 r.n_wunits = (r.n_items + G - 1) / G;
+                r.gsize = G;
                 r.prev = (k > k_lo) ? (int32_t)recs.size() - 1 : -1;
-                int u = u0;
-                for (int64_t i = 0; i < r.n_items; ++i) {
-                    const int64_t q = P0 + i * C;
-                    while (g.apair[(size_t)u + 1] <= q) ++u;
-                    items.push_back(u);
-                }
                 // combine-tree scratch of this minibatch (see f2v_internal.h)
                 r.slot_off = slot_total;
                 r.cnt_off = cnt_total;
@@ -485,12 +519,13 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
     } catch (const std::bad_alloc &) {
         return fail(F2V_ENOMEM, "host allocation failed (batch tables)");
     }
-    if (items.size() >= (size_t)INT32_MAX)
+    if (item_total >= (int64_t)INT32_MAX)
         return fail(F2V_EINVAL, "the batch holds 2^31 or more items; use a larger item size");
     n_recs_ = (int)recs.size();
 
-    // one queue per shape present: its records by k / M_g, then graph
-    std::vector<BatchUnit> units;
+    // one queue per shape present: its records by k / M_g, then graph; the
+    // records' warp units are laid out in that order
+    int64_t unit_total = 0;
     for (int sh = 0; sh < kNumBatchShapes; ++sh) {
         std::vector<int> rs;
         double weight = 0.0;
@@ -506,16 +541,18 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
         });
         Queue q;
         q.shape = sh;
-        q.unit_off = (int64_t)units.size();
+        q.unit_off = unit_total;
         q.weight = weight;
-        const int G = 32 / kBatchShapes[sh].L;
         for (int i : rs) {
-            const BatchRec &r = recs[(size_t)i];
-            for (int w = 0; w < r.n_wunits; ++w) units.push_back(BatchUnit{i, w * G});
+            BatchRec &r = recs[(size_t)i];
+            r.unit_off = (int32_t)std::min<int64_t>(unit_total, INT32_MAX);
+            unit_total += r.n_wunits;
         }
-        q.n_units = (int32_t)((int64_t)units.size() - q.unit_off);
+        q.n_units = (int32_t)std::min<int64_t>(unit_total - q.unit_off, INT32_MAX);
         queues_.push_back(q);
     }
+    if (unit_total >= (int64_t)INT32_MAX)
+        return fail(F2V_EINVAL, "the batch holds 2^31 or more work units; use a larger item size");
     // grids: every launch of the epoch runs at once, sized by its share of
     // the work, so each graph's minibatches spread over the whole epoch
     double wsum = 0.0;
@@ -530,21 +567,26 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
     }
 
     f2v_status st;
+    const size_t R = recs.size();
     if ((st = grow((void **)&d_graphs_, &cap_graphs_, sizeof(BatchGraph) * P)) != F2V_OK) return st;
     if ((st = grow((void **)&d_state_, &cap_state_, sizeof(BatchState) * P)) != F2V_OK) return st;
-    if ((st = grow((void **)&d_recs_, &cap_recs_, sizeof(BatchRec) * recs.size())) != F2V_OK) return st;
-    if ((st = grow((void **)&d_units_, &cap_units_, sizeof(BatchUnit) * units.size())) != F2V_OK) return st;
-    if ((st = grow((void **)&d_item_u0_, &cap_items_, sizeof(int32_t) * items.size())) != F2V_OK) return st;
+    if ((st = grow((void **)&d_recs_, &cap_recs_, sizeof(BatchRec) * R)) != F2V_OK) return st;
+    if ((st = grow((void **)&d_units_, &cap_units_, sizeof(BatchUnit) * (size_t)unit_total)) != F2V_OK) return st;
+    if ((st = grow((void **)&d_item_u0_, &cap_items_, sizeof(int32_t) * (size_t)item_total)) != F2V_OK) return st;
     if ((st = grow((void **)&d_slots_, &cap_slots_, sizeof(float) * (size_t)slot_total)) != F2V_OK) return st;
     if ((st = grow((void **)&d_cnt_, &cap_cnt_, sizeof(int32_t) * (size_t)cnt_total)) != F2V_OK) return st;
-    if ((st = grow((void **)&d_done_, &cap_done_, sizeof(int32_t) * recs.size())) != F2V_OK) return st;
+    if ((st = grow((void **)&d_done_, &cap_done_, sizeof(int32_t) * R)) != F2V_OK) return st;
     if ((st = grow((void **)&d_next_, &cap_next_, sizeof(int32_t) * queues_.size())) != F2V_OK) return st;
     ENG_CUDA(cudaMemcpyAsync(d_graphs_, hg.data(), sizeof(BatchGraph) * P, cudaMemcpyHostToDevice, stream_));
     ENG_CUDA(cudaMemcpyAsync(d_state_, hs.data(), sizeof(BatchState) * P, cudaMemcpyHostToDevice, stream_));
-    ENG_CUDA(cudaMemcpyAsync(d_recs_, recs.data(), sizeof(BatchRec) * recs.size(), cudaMemcpyHostToDevice, stream_));
-    ENG_CUDA(cudaMemcpyAsync(d_units_, units.data(), sizeof(BatchUnit) * units.size(), cudaMemcpyHostToDevice, stream_));
-    ENG_CUDA(cudaMemcpyAsync(d_item_u0_, items.data(), sizeof(int32_t) * items.size(), cudaMemcpyHostToDevice, stream_));
+    ENG_CUDA(cudaMemcpyAsync(d_recs_, recs.data(), sizeof(BatchRec) * R, cudaMemcpyHostToDevice, stream_));
     ENG_CUDA(cudaMemsetAsync(d_cnt_, 0, std::max<size_t>(16, sizeof(int32_t) * (size_t)cnt_total), stream_));
+    if (R > 0) {
+        batch_expand_kernel<<<(int)std::min<size_t>(R, 8192), 128, 0, stream_>>>(
+            d_graphs_, d_recs_, (int)R, d_item_u0_, d_units_);
+        ENG_CUDA(cudaGetLastError());
+        ++launches_;
+    }
     // pageable sources: the copies have read them when they return
     return capture(k_hi >= max_minibatches());
 }

@@ -44,7 +44,8 @@ public:
     // drawn from `seed` on the engine's stream; returns its id (>= 0) or -1
     // with err() set.  The graph joins from the next epoch.
     int add_graph(const int32_t *row_ptr, const int32_t *col_idx, int n, int d, uint64_t seed,
-                  float lr, int schedule, int total_epochs, f2v_status *st);
+                  float lr, int schedule, int total_epochs, f2v_status *st,
+                  bool validated = false);
     // Removes a graph after the work enqueued so far (synchronises).
     f2v_status remove_graph(int id);
 
@@ -84,8 +85,10 @@ public:
     bool failed() const { return failed_; }
     const std::string &err() const { return err_; }
     f2v_status fail(f2v_status st, const char *fmt, ...);
-    // Device bytes graph of size (n, d, nnz) would take (for admission).
+    // Device bytes a graph of size (n, d, nnz) takes (its arrays, plus the
+    // work tables and combine-tree scratch of its pairs): for admission.
     size_t graph_bytes(int64_t n, int d, int64_t nnz) const;
+    size_t table_bytes(int64_t pairs, int64_t n, int d) const;
 
 private:
     struct Graph {

@@ -200,6 +200,8 @@ struct BatchRec {
     int32_t item_off;          // its items' start vertices in BatchArgs::item_u0
     int32_t n_wunits;          // warp units of this minibatch
     int32_t prev;              // record of minibatch k - 1 of graph g, or -1
+    int32_t unit_off;          // its first warp unit in the unit table
+    int32_t gsize;             // items per warp unit (32 / L)
     int32_t pad;
 };
 

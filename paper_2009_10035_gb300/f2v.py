@@ -121,6 +121,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_batch_launch_count": ([vp, ctypes.POINTER(i64)], st),
             "f2v_batch_stream": ([vp, pp], st),
             "f2v_batch_last_error": ([vp], ctypes.c_char_p),
+            # served form (include/f2v_serve.h)
+            "f2v_server_create": ([sz, i32, pp], st),
+            "f2v_server_submit": ([vp, vp, ctypes.POINTER(i64)], st),
+            "f2v_server_job": ([vp, i64, vp], st),
+            "f2v_server_wait": ([vp, i64], st),
+            "f2v_server_wait_all": ([vp], st),
+            "f2v_server_get_stats": ([vp, vp], st),
+            "f2v_server_destroy": ([vp], None),
+            "f2v_server_last_error": ([vp], ctypes.c_char_p),
+            "f2v_server_job_error": ([vp, i64], ctypes.c_char_p),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -477,3 +487,114 @@ class Batch:
         v = ctypes.c_void_p()
         self._check(self._lib.f2v_batch_stream(self._h, ctypes.byref(v)))
         return v.value or 0
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = range(4)
+
+
+class JobSpec(ctypes.Structure):
+    """f2v_job."""
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("n", ctypes.c_int32), ("d", ctypes.c_int32), ("model", ctypes.c_int),
+                ("s", ctypes.c_int32), ("lr", ctypes.c_float), ("minibatch", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("epochs", ctypes.c_int32),
+                ("precision", ctypes.c_int), ("out", ctypes.c_void_p)]
+
+
+class JobInfo(ctypes.Structure):
+    """f2v_job_info."""
+    _fields_ = [("state", ctypes.c_int32), ("epochs_done", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("finish_s", ctypes.c_double), ("pairs", ctypes.c_int64),
+                ("device_bytes", ctypes.c_size_t), ("status", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    """f2v_server_stats."""
+    _fields_ = [("submitted", ctypes.c_int64), ("done", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("pairs_done", ctypes.c_int64), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("budget", ctypes.c_size_t),
+                ("busy_s", ctypes.c_double)]
+
+
+class Server:
+    """Job server with continuous batching (include/f2v_serve.h).  The arrays
+    of a submitted job are kept alive here until the job is collected."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 1 << 20):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        rc = self._lib.f2v_server_create(int(budget_bytes), int(max_active), ctypes.byref(h))
+        if rc != OK:
+            raise F2VError(rc, self._lib.f2v_last_error_global().decode())
+        self._h = h
+        self._keep = {}
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise F2VError(rc, self._lib.f2v_server_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.f2v_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, row_ptr, col_idx, n: int, d: int, model: int = TDIST, s: int = 5,
+               lr: float = 0.02, minibatch: int = 4096, seed: int = 1, epochs: int = 10,
+               precision: int = FP32, out: np.ndarray | None = None) -> int:
+        """Enqueues a job; returns its id.  `out` (n x d float32, C order)
+        receives Z when the job completes (allocated here if not given)."""
+        rp = np.ascontiguousarray(row_ptr, np.int32)
+        ci = np.ascontiguousarray(col_idx, np.int32)
+        if ci.size == 0:
+            ci = np.zeros(1, np.int32)
+        if out is None:
+            out = np.empty((int(n), int(d)), np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size >= int(n) * int(d)
+        spec = JobSpec(_ptr(rp).value, _ptr(ci).value, int(n), int(d), int(model), int(s),
+                       float(lr), int(minibatch), int(seed) & (2**64 - 1), int(epochs),
+                       int(precision), _ptr(out).value)
+        jid = ctypes.c_int64()
+        self._check(self._lib.f2v_server_submit(self._h, ctypes.byref(spec), ctypes.byref(jid)))
+        self._keep[jid.value] = (rp, ci, out)
+        return jid.value
+
+    def info(self, jid: int) -> JobInfo:
+        info = JobInfo()
+        self._check(self._lib.f2v_server_job(self._h, int(jid), ctypes.byref(info)))
+        return info
+
+    def wait(self, jid: int) -> np.ndarray:
+        """Waits for job `jid` and returns its Z (raises if it failed)."""
+        rc = self._lib.f2v_server_wait(self._h, int(jid))
+        if rc != OK:
+            raise F2VError(rc, self._lib.f2v_server_job_error(self._h, int(jid)).decode())
+        rp, ci, out = self._keep.pop(int(jid))
+        return out
+
+    def wait_all(self):
+        self._lib.f2v_server_wait_all(self._h)
+
+    def forget(self, jid: int):
+        """Drops the references kept for a finished job."""
+        self._keep.pop(int(jid), None)
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        self._check(self._lib.f2v_server_get_stats(self._h, ctypes.byref(st)))
+        return st
