@@ -442,6 +442,7 @@ void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochA
     ea.mb_C = c->d_mb_C;
     ea.row_flag = c->row_flag;
     ea.mb_done = c->mb_done;
+    ea.mb_next = c->mb_done + c->mb_C.size();
     ea.slots = c->slots;
     ea.unit_cnt = c->unit_cnt;
     ea.slot_stride = c->slot_stride;
@@ -475,6 +476,9 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     }
     if (c->bulk)
         F2V_CUDA(c, cudaMemsetAsync(c->mb_done + k_begin, 0,
+                                    sizeof(int32_t) * (size_t)(k_end - k_begin), c->stream));
+    if (c->bulk)
+        F2V_CUDA(c, cudaMemsetAsync(c->mb_done + c->mb_C.size() + k_begin, 0,
                                     sizeof(int32_t) * (size_t)(k_end - k_begin), c->stream));
     for (int k = k_begin; k < k_end; k += step) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -691,7 +695,7 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         st = alloc(c, (void **)&c->d_mb_item_base, sizeof(int64_t) * (M + 1));
         if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
         if (st == F2V_OK) st = alloc(c, (void **)&c->row_flag, sizeof(int32_t) * (size_t)n);
-        if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * M);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * 2 * M);
         if (st == F2V_OK)
             st = alloc(c, (void **)&c->partner, sizeof(int32_t) * (size_t)c->h_apair[(size_t)n]);
         std::string merr;
@@ -736,7 +740,7 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         CREATE_CUDA(cudaMemcpyAsync(c->d_mb_C, c->mb_C.data(), sizeof(int32_t) * M,
                                     cudaMemcpyHostToDevice, c->stream));
         CREATE_CUDA(cudaMemsetAsync(c->row_flag, 0, sizeof(int32_t) * (size_t)n, c->stream));
-        CREATE_CUDA(cudaMemsetAsync(c->mb_done, 0, sizeof(int32_t) * M, c->stream));
+        CREATE_CUDA(cudaMemsetAsync(c->mb_done, 0, sizeof(int32_t) * 2 * M, c->stream));
     }
     CREATE_CUDA(launch_init(c));
     CREATE_CUDA(cudaStreamSynchronize(c->stream));

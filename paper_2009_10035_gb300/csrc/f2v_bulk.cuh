@@ -3,15 +3,16 @@
 // TMA bulk copies.  One launch runs a range of minibatches of one epoch.
 //
 // Work.  Minibatch k's pair sequence (neighbours of each vertex in CSR
-// order, then its s negative samples) is cut into one contiguous chunk per
-// warp; warp w takes chunk w of every minibatch, in minibatch order, and
-// flows from one minibatch into the next without a grid-wide barrier.  Per
-// tile of at most 32 pairs spanning at most 8 vertices:
-//   decode  lane t finds pair t's vertex and partner (col_idx or Philox);
-//   stage   lane t issues one cp.async.bulk copy of its partner row into the
-//           warp's shared buffer, lanes j < 8 copy the tile's own rows, all
-//           completing on one mbarrier; the next tile (possibly of the next
-//           minibatch) is decoded while the copies are in flight;
+// order, then its s negative samples) is cut into chunks of C_k pairs (about
+// one per warp); a free warp takes the next unclaimed chunk of the oldest
+// minibatch that has one left, so warps flow from one minibatch into the next
+// without a grid-wide barrier, and a slow chunk holds up no warp but its own.
+// Per tile of at most 32 pairs spanning at most 8 vertices:
+//   decode  lane t finds pair t's vertex and partner (the epoch's partner list);
+//   stage   TMA gather4 copies bring the tile's partner rows and own rows
+//           into the warp's shared buffers, completing on one mbarrier; the
+//           next tile (possibly of the next chunk) is decoded while the
+//           copies are in flight;
 //   reduce  each lane forms the partial dot product / squared distance of
 //           all 32 rows over its EPL elements, and a transpose-reduction
 //           (31 shuffles) leaves lane r with row r's full sum;
@@ -23,11 +24,12 @@
 // Ordering between minibatches (synchronous SGD, Sec. III-B).  A partner row
 // v of an earlier minibatch is read from the next buffer only after its
 // flag row_flag[v] equals epoch + 1, which its writer releases after the row
-// is stored.  A warp checks those flags only after finishing its own chunk
-// of the previous minibatch, so the warp on the oldest minibatch always
-// progresses.  The combine-tree scratch is a ring of `ring` regions; before
-// starting minibatch k a warp waits until minibatch k - ring is complete.
-// All warps of the grid must be resident at once (one block per SM).
+// is stored.  A warp holds one chunk at a time and waits only for rows of
+// older minibatches, whose chunks were all claimed by running warps, so the
+// oldest unfinished chunk always progresses (no block needs to wait for a
+// block that is not resident).  The combine-tree scratch is a ring of `ring`
+// regions; before claiming a chunk of minibatch k a warp waits until
+// minibatch k - ring is complete.
 //
 // Every wait is bounded (about a second at 2 GHz): on expiry the kernel
 // records an error code (1 mbarrier, 2 row flag, 3 ring), lets its own copies
@@ -143,6 +145,7 @@ struct BulkLayout {
 
 // One chunk of one minibatch.
 struct Chunk {
+    int idx;               // chunk index within the minibatch
     int k;                 // minibatch
     int mb_begin;          // its first vertex
     int64_t P0;            // its first pair (global index)
@@ -151,14 +154,21 @@ struct Chunk {
     int u0;                // vertex holding pair q_begin
 };
 
-// First chunk of warp w in a minibatch >= k of the launch; false if none.
+// Takes the next unclaimed chunk of the first minibatch >= k of the launch
+// that has one left (a per-minibatch counter hands chunks out in order);
+// false if none.  Whichever warp is free takes the next chunk, so a slow
+// chunk delays its own minibatch only, not every later one.
 template <typename Ts>
-__device__ __forceinline__ bool find_chunk(const EpochArgs<Ts> &a, int w, int k, Chunk &c)
+__device__ __forceinline__ bool find_chunk(const EpochArgs<Ts> &a, int lane, int k, Chunk &c)
 {
     for (; k < a.k_end; ++k) {
         const int64_t base = __ldg(&a.mb_item_base[k]);
         const int64_t nch = __ldg(&a.mb_item_base[k + 1]) - base;
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&a.mb_next[k], 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
         if (w < nch) {
+            c.idx = w;
             c.k = k;
             c.mb_begin = k * a.b;
             const int mb_end = min(a.f.n, c.mb_begin + a.b);
@@ -249,8 +259,6 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int warps = blockDim.x >> 5;
-    const int w = blockIdx.x * warps + warp;        // this warp's chunk in every minibatch
     unsigned char *wsm = smem_raw + (size_t)warp * Lay::BYTES;
     Ts *rows = reinterpret_cast<Ts *>(wsm + Lay::ROWS_OFF);
     float *own = reinterpret_cast<float *>(wsm + Lay::OWN_OFF);
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
     uint32_t phase = 0;
 
     Chunk ch;
-    if (!find_chunk(a, w, a.k_begin, ch)) return;
+    if (!find_chunk(a, lane, a.k_begin, ch)) return;
     Tile t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
     bool chunk_start = true;
     int ucur = -1, vbeg = 0, vend = 0;
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
         bool more = true;
         if (!last_of_chunk) {
             t = decode_tile(a, cur, q_next, t.u_next, lane);
-        } else if (find_chunk(a, w, cur.k + 1, ch)) {
+        } else if (find_chunk(a, lane, cur.k, ch)) {
             t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
         } else {
             more = false;
@@ -468,7 +476,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
             const int j = vert[rs];
             if (tu + j != ucur) {
                 if (ucur >= 0)
-                    finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, w, ucur, vbeg,
+                    finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg,
                                                      vend, zu, g);
                 vbeg = (ucur >= 0) ? vend : first_lo;
                 ucur = tu + j;
@@ -528,7 +536,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
         }
         if (last_of_chunk) {
             // the chunk's last vertex, then the chunk counts as done
-            finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, w, ucur, vbeg, vend, zu,
+            finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg, vend, zu,
                                              g);
             ucur = -1;
             __syncwarp();

@@ -83,6 +83,7 @@ struct EpochArgs {
     const int32_t *mb_C;           // M: pairs per chunk of each minibatch
     int32_t *row_flag;             // n: epoch + 1 once row v is written this epoch
     int32_t *mb_done;              // M: chunks finished (zeroed before the launch)
+    int32_t *mb_next;              // M: chunks claimed (zeroed before the launch)
     float *slots;                  // ring regions of combine-tree slots
     int32_t *unit_cnt;             // ring regions of combine-tree counters
     int64_t slot_stride, cnt_stride;
