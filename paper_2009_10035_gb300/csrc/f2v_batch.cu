@@ -137,6 +137,17 @@ namespace {
 // Default pairs per item: long enough to amortise the item's set-up, short
 // enough that a minibatch of b vertices spreads over many groups.
 int default_item_pairs(int d) { return d <= 8 ? 128 : 256; }
+
+// Relative GPU time of one pair in a shape's kernel, used to split the SMs
+// between the concurrent launches of an epoch so that they end together.
+// Measured on the 4,096-graph SBM workload with each row size alone: a
+// one-lane shape (L = 1) pays a whole decode per pair (~75); wider shapes pay
+// a shared decode plus the row (~30 + d).
+double pair_cost(int shape)
+{
+    const BatchShape &s = kBatchShapes[shape];
+    return s.L == 1 ? 75.0 : 30.0 + (double)s.d;
+}
 }  // namespace
 
 BatchEngine::~BatchEngine()
@@ -532,7 +543,7 @@ f2v_status BatchEngine::rebuild(int k_lo, int k_hi)
         for (int i = 0; i < n_recs_; ++i)
             if (hg[(size_t)recs[(size_t)i].g].shape == sh) {
                 rs.push_back(i);
-                weight += (double)recs[(size_t)i].Pk * (hg[(size_t)recs[(size_t)i].g].d + 8);
+                weight += (double)recs[(size_t)i].Pk * pair_cost(sh);
             }
         if (rs.empty()) continue;
         std::stable_sort(rs.begin(), rs.end(), [&](int a, int b) {
