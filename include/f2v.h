@@ -12,7 +12,10 @@
  *   F2V_TDIST    t-distribution similarity, Eq. 7; gradients Eq. 8 / Eq. 9
  *                times the unit vector (z_u - z_x)/t of Sec. III-B.  t^2 is
  *                floored at 1e-8 in the repulsive term.
- *   F2V_SIGMOID  sigmoid of the dot product, Eq. 3; gradients Eq. 5 / Eq. 6.
+ *   F2V_SIGMOID  sigmoid of the dot product, Eq. 3; gradients Eq. 5 / Eq. 6;
+ *                after each update the coordinates of z_u are clamped to
+ *                [-4, 4] (the paper is silent; unbounded, the summed
+ *                gradients of high-degree vertices make the run diverge).
  *
  * Conventions shared by every entry point:
  *   - All functions return f2v_status and never abort.  A failure leaves a

@@ -41,6 +41,11 @@
  *   - t model: t^2 is clamped to at least 1e-8 in the repulsive term only.
  *   - Learning-rate schedule: constant, or eta_e = eta0 * (1 - e/E) for a
  *     linearly decayed run of E epochs.
+ *   - Sigmoid model: after each update every coordinate of z_u is clamped to
+ *     [-4, 4].  The paper is silent on divergence; without a bound, Alg. 1 at
+ *     eta = 0.02 with the summed gradients of Alg. 2 diverges on graphs with
+ *     high-degree vertices even in FP64 (max |z| grows ~1e5-fold per epoch on
+ *     an R-MAT scale-20 graph), leaving FP32's range after seven epochs.
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +59,7 @@
 #define ORC_SIGMOID 1
 
 #define ORC_T2_FLOOR 1e-8
+#define ORC_SIGMOID_BOUND 4.0
 
 /* OpenMP thread count used by the parallel loops (n <= 0: leave as is). */
 int orc_set_threads(int n)
@@ -336,8 +342,14 @@ int orc_train(int model, int64_t n, int32_t d,
             orc_grad_minibatch(model, n, d, row_ptr, col_idx, Z, u0, u1, s, seed, e,
                                samp_ptr, samp_idx, grad);
             for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
-                for (int32_t j = 0; j < d; ++j)
-                    Z[u * d + j] = Z[u * d + j] - eta * grad[(u - u0) * d + j];
+                for (int32_t j = 0; j < d; ++j) {
+                    double z = Z[u * d + j] - eta * grad[(u - u0) * d + j];
+                    if (model == ORC_SIGMOID) {              /* bounded coordinates */
+                        if (z > ORC_SIGMOID_BOUND) z = ORC_SIGMOID_BOUND;
+                        if (z < -ORC_SIGMOID_BOUND) z = -ORC_SIGMOID_BOUND;
+                    }
+                    Z[u * d + j] = z;
+                }
         }
     }
     free(grad);

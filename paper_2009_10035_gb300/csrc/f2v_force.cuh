@@ -37,6 +37,7 @@ constexpr int KIND_NONE = 0;   // no force (self sample, or the empty pair)
 constexpr int KIND_ATTR = 1;   // neighbour: attractive force
 constexpr int KIND_REP = 2;    // negative sample: repulsive force
 constexpr float kT2Floor = 1e-8f;
+constexpr float kSigmoidBound = 4.f;
 
 template <int L, int VEC, int NV>
 struct ShapeTraits {
@@ -136,6 +137,12 @@ __device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, const FinishCt
     float z[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) z[e] = fmaf(-a.eta, g[e], zu[e]);
+    if (a.model == 1) {
+        // sigmoid model: coordinates bounded to [-4, 4] (without a bound the
+        // summed gradients of a high-degree vertex make Alg. 1 diverge)
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[e] = fminf(fmaxf(z[e], -kSigmoidBound), kSigmoidBound);
+    }
     Ts *dst = a.znext + (int64_t)u * a.ld;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {

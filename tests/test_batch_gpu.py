@@ -91,6 +91,8 @@ def check_step(bt, glist, dims, seeds, model, s, b, lr, e, k, before, which,
         G, A = oracle.grad_minibatch_abs(model, g.row_ptr, g.col_idx, before[i], u0, u1, s,
                                          int(seeds[i]), e)
         want = before[i][u0:u1] - eta * G
+        if model == f2v.SIGMOID:
+            want = np.clip(want, -4.0, 4.0)
         scale = np.maximum(np.abs(before[i][u0:u1]) + eta * A, FLOOR)
         err = np.abs(after[u0:u1] - want) / scale
         assert np.isfinite(after).all()

@@ -394,3 +394,24 @@ def test_philox_self_samples_are_skipped():
         inj = [[int(w) for w in S[u] if w != u] for u in range(n)]
         Gi = oracle.grad_minibatch(m, g.row_ptr, g.col_idx, Z, 0, n, 0, seed, 0, injected=inj)
         np.testing.assert_array_equal(G, Gi)
+
+
+def test_sigmoid_coordinates_are_bounded_t_model_is_not():
+    """Sigmoid model: each coordinate of an updated row is clamped to [-4, 4]
+    (worked by hand: one edge, s = 0, b = 2, eta = 10, d = 1, z = (3.9, 0.1);
+    grad_u = (sigma(0.39) - 1) * 0.1, grad_v = (sigma(0.39) - 1) * 3.9, both
+    negative, so both rows move up past 4 and stop there).  The t model is not
+    bounded: z_v = 0.1 + 10 * 2 * 3.8 / (1 + 3.8^2) = 5.0223..."""
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    Z0 = np.array([[3.9], [0.1]])
+    zs = oracle.train(1, rp, ci, Z0, 0, 2, 1, 10.0, 1)
+    assert zs[0, 0] == 4.0 and zs[1, 0] == 4.0
+    zt = oracle.train(0, rp, ci, Z0, 0, 2, 1, 10.0, 1)
+    step = 10.0 * 2.0 * 3.8 / (1.0 + 3.8 ** 2)
+    assert abs(zt[0, 0] - (3.9 - step)) < 1e-12
+    assert abs(zt[1, 0] - (0.1 + step)) < 1e-12 and zt[1, 0] > 4.0
+    # below the bound the update is the plain Eq. 10 step
+    zs2 = oracle.train(1, rp, ci, np.array([[0.3], [-0.2]]), 0, 2, 1, 0.5, 1)
+    g_u = (1.0 / (1.0 + math.exp(0.06)) - 1.0) * -0.2
+    assert abs(zs2[0, 0] - (0.3 - 0.5 * g_u)) < 1e-12

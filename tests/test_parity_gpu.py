@@ -97,6 +97,8 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
                 eta = oracle.learning_rate(lr, 0 if schedule is None else schedule,
                                            total_epochs, e)
                 want = before[u0:u1] - eta * G
+                if model == f2v.SIGMOID:
+                    want = np.clip(want, -4.0, 4.0)
                 scale = np.maximum(np.abs(before[u0:u1]) + eta * A, FLOOR)
                 err = np.abs(after[u0:u1] - want) / scale
                 assert np.isfinite(after).all()
