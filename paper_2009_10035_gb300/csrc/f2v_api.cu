@@ -494,7 +494,7 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
                 EpochArgs<__nv_bfloat16> ea{};
                 fill_epoch_args(c, k, k + step, eta, ea);
                 ea.f.master = c->master;
-                err = launch_bulk_bf16(c->d, ea, c->zmap, c->mmap, c->bulk_sms, c->bulk_warps,
+                err = launch_bulk_bf16(c->d, c->model, ea, c->zmap, c->mmap, c->bulk_sms, c->bulk_warps,
                                        c->bulk_smem, c->stream);
             } else {
                 ForceArgs<__nv_bfloat16> a{};
@@ -507,7 +507,7 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
                 EpochArgs<float> ea{};
                 fill_epoch_args(c, k, k + step, eta, ea);
                 ea.f.master = nullptr;
-                err = launch_bulk_fp32(c->d, ea, c->zmap, c->zmap, c->bulk_sms, c->bulk_warps,
+                err = launch_bulk_fp32(c->d, c->model, ea, c->zmap, c->zmap, c->bulk_sms, c->bulk_warps,
                                        c->bulk_smem, c->stream);
             } else {
                 ForceArgs<float> a{};

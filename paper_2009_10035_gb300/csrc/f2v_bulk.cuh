@@ -36,6 +36,7 @@
 // land, and returns; the host reports F2V_ETIMEOUT.
 #pragma once
 
+#include <algorithm>
 #include <climits>
 
 #include "f2v_device.cuh"
@@ -245,7 +246,7 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
     return t;
 }
 
-template <int D, typename Ts>
+template <int D, typename Ts, int MODEL>
 __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
     int *vert = reinterpret_cast<int *>(wsm + Lay::VERT_OFF);
     int *vends = reinterpret_cast<int *>(wsm + Lay::VEND_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + Lay::BAR_OFF);
-    const bool tdist = (a.f.model == 0);
+    constexpr bool tdist = (MODEL == 0);            // the force model, fixed per instantiation
     const int flag_value = (int)a.f.epoch + 1;
 
     // zero the staging buffers once, so rows that are never copied are finite
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
             const int j = vert[rs];
             if (tu + j != ucur) {
                 if (ucur >= 0)
-                    finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg,
+                    finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg,
                                                      vend, zu, g);
                 vbeg = (ucur >= 0) ? vend : first_lo;
                 ucur = tu + j;
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
         }
         if (last_of_chunk) {
             // the chunk's last vertex, then the chunk counts as done
-            finish_vertex<32, VEC, NV, true>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg, vend, zu,
+            finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg, vend, zu,
                                              g);
             ucur = -1;
             __syncwarp();
@@ -572,28 +573,29 @@ bool bulk_config_t(int d, int *warps, int *smem)
 }
 
 // Blocks of `warps` warps that fit on one SM at once (0 if none).
-template <int D, typename Ts>
+template <int D, typename Ts, int MODEL>
 int bulk_resident_d(int warps, int smem)
 {
-    if (cudaFuncSetAttribute(force_bulk_kernel<D, Ts>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, force_bulk_kernel<D, Ts>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, force_bulk_kernel<D, Ts, MODEL>,
                                                       warps * 32, smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
-template <int D, typename Ts>
+template <int D, typename Ts, int MODEL>
 cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const CUtensorMap &mmap,
                           int blocks, int warps, int smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts>,
+    cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    // Warps wait on rows and chunks that other blocks produce, so every block
-    // must be resident at once: a cooperative launch guarantees that or fails.
+    // Warps wait on rows and chunks that other blocks produce; a cooperative
+    // launch places every block at once (or fails) so that no wait can be
+    // on a block that has not started.
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3((unsigned)(warps * 32));
@@ -604,31 +606,45 @@ cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, force_bulk_kernel<D, Ts>, a, zmap, mmap);
+    e = cudaLaunchKernelEx(&cfg, force_bulk_kernel<D, Ts, MODEL>, a, zmap, mmap);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <typename Ts>
-cudaError_t launch_bulk_t(int d, const EpochArgs<Ts> &a, const CUtensorMap &zmap,
+cudaError_t launch_bulk_t(int d, int model, const EpochArgs<Ts> &a, const CUtensorMap &zmap,
                           const CUtensorMap &mmap, int blocks, int warps, int smem,
                           cudaStream_t st)
 {
+    const bool t = (model == 0);
     switch (d) {
-        case 64: return launch_bulk_d<64, Ts>(a, zmap, mmap, blocks, warps, smem, st);
-        case 128: return launch_bulk_d<128, Ts>(a, zmap, mmap, blocks, warps, smem, st);
-        case 256: return launch_bulk_d<256, Ts>(a, zmap, mmap, blocks, warps, smem, st);
+        case 64:
+            return t ? launch_bulk_d<64, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
+                     : launch_bulk_d<64, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
+        case 128:
+            return t ? launch_bulk_d<128, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
+                     : launch_bulk_d<128, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
+        case 256:
+            return t ? launch_bulk_d<256, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
+                     : launch_bulk_d<256, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
+// Blocks per SM: the smaller of the two models' (they differ only in code).
 template <typename Ts>
 int bulk_resident_t(int d, int warps, int smem)
 {
     switch (d) {
-        case 64: return bulk_resident_d<64, Ts>(warps, smem);
-        case 128: return bulk_resident_d<128, Ts>(warps, smem);
-        case 256: return bulk_resident_d<256, Ts>(warps, smem);
+        case 64:
+            return std::min(bulk_resident_d<64, Ts, 0>(warps, smem),
+                            bulk_resident_d<64, Ts, 1>(warps, smem));
+        case 128:
+            return std::min(bulk_resident_d<128, Ts, 0>(warps, smem),
+                            bulk_resident_d<128, Ts, 1>(warps, smem));
+        case 256:
+            return std::min(bulk_resident_d<256, Ts, 0>(warps, smem),
+                            bulk_resident_d<256, Ts, 1>(warps, smem));
         default: return 0;
     }
 }

@@ -128,7 +128,9 @@ __device__ __forceinline__ void publish_row(int32_t *flag, int u, int32_t value,
 }
 
 // z_u <- z_u - eta * g (Eq. 10) into the next buffer (and the master).
-template <int L, int VEC, int NV, bool EXACT, typename Ts>
+// MODEL: the force model when the caller fixes it at compile time (0 t,
+// 1 sigmoid), else -1 (read from a.model).
+template <int L, int VEC, int NV, bool EXACT, int MODEL = -1, typename Ts>
 __device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, const FinishCtx &fc,
                                           unsigned gmask, int u, int gl, const float *zu,
                                           const float *g)
@@ -137,9 +139,9 @@ __device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, const FinishCt
     float z[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) z[e] = fmaf(-a.eta, g[e], zu[e]);
-    if (a.model == 1) {
-        // sigmoid model: coordinates bounded to [-4, 4] (without a bound the
-        // summed gradients of a high-degree vertex make Alg. 1 diverge)
+    // sigmoid model: coordinates bounded to [-4, 4] (without a bound the
+    // summed gradients of a high-degree vertex make Alg. 1 diverge)
+    if (MODEL == 1 || (MODEL < 0 && a.model == 1)) {
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = fminf(fmaxf(z[e], -kSigmoidBound), kSigmoidBound);
     }
@@ -167,7 +169,7 @@ __device__ __forceinline__ int64_t unit_slot(int64_t j, int lb, int64_t unit_pai
 // level-0 unit `unit0` are summed in g: writes z_u - eta * g if the unit held
 // all of them, else passes the part up the ordered combine tree (g is
 // clobbered).
-template <int L, int VEC, int NV, bool EXACT, typename Ts>
+template <int L, int VEC, int NV, bool EXACT, int MODEL = -1, typename Ts>
 __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const FinishCtx &fc,
                                               unsigned gmask, int gl, int unit0, int u, int vbeg,
                                               int vend, const float *zu, float *g)
@@ -175,7 +177,7 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const Fini
     constexpr int E = VEC * NV;
     int64_t fu = vbeg / fc.C, lu = (vend - 1) / fc.C;
     if (fu == lu) {
-        write_row<L, VEC, NV, EXACT>(a, fc, gmask, u, gl, zu, g);
+        write_row<L, VEC, NV, EXACT, MODEL>(a, fc, gmask, u, gl, zu, g);
         return;
     }
     int64_t unit = unit0, unit_pairs = fc.C, units = a.units0;
@@ -223,7 +225,7 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const Fini
         }
         if (gl == 0) *cnt = 0;
         if (top) {
-            write_row<L, VEC, NV, EXACT>(a, fc, gmask, u, gl, zu, g);
+            write_row<L, VEC, NV, EXACT, MODEL>(a, fc, gmask, u, gl, zu, g);
             return;
         }
         slot_base += 2 * units * a.ld;

@@ -11,11 +11,11 @@ cudaError_t launch_force_bf16(const Shape &sh, const ForceArgs<__nv_bfloat16> &a
     return launch_force_any<__nv_bfloat16>(sh, a, blocks_cap, st);
 }
 
-cudaError_t launch_bulk_bf16(int d, const EpochArgs<__nv_bfloat16> &a, const CUtensorMap &zmap,
-                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
-                             cudaStream_t st)
+cudaError_t launch_bulk_bf16(int d, int model, const EpochArgs<__nv_bfloat16> &a,
+                             const CUtensorMap &zmap, const CUtensorMap &mmap, int blocks,
+                             int warps, int smem_bytes, cudaStream_t st)
 {
-    return launch_bulk_t<__nv_bfloat16>(d, a, zmap, mmap, blocks, warps, smem_bytes, st);
+    return launch_bulk_t<__nv_bfloat16>(d, model, a, zmap, mmap, blocks, warps, smem_bytes, st);
 }
 
 }  // namespace f2v

@@ -10,11 +10,11 @@ cudaError_t launch_force_fp32(const Shape &sh, const ForceArgs<float> &a, int bl
     return launch_force_any<float>(sh, a, blocks_cap, st);
 }
 
-cudaError_t launch_bulk_fp32(int d, const EpochArgs<float> &a, const CUtensorMap &zmap,
-                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
-                             cudaStream_t st)
+cudaError_t launch_bulk_fp32(int d, int model, const EpochArgs<float> &a,
+                             const CUtensorMap &zmap, const CUtensorMap &mmap, int blocks,
+                             int warps, int smem_bytes, cudaStream_t st)
 {
-    return launch_bulk_t<float>(d, a, zmap, mmap, blocks, warps, smem_bytes, st);
+    return launch_bulk_t<float>(d, model, a, zmap, mmap, blocks, warps, smem_bytes, st);
 }
 
 int bulk_resident(int d, bool bf16, int warps, int smem_bytes)

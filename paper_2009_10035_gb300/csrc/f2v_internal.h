@@ -130,12 +130,13 @@ bool bulk_config(int d, bool bf16, int *warps_per_block, int *smem_bytes);
 int bulk_resident(int d, bool bf16, int warps, int smem_bytes);
 // `zmap` covers both Z buffers (2n rows of the storage type); `mmap` the FP32
 // own rows (the master in the BF16 form, zmap again in the FP32 form).
-cudaError_t launch_bulk_fp32(int d, const EpochArgs<float> &a, const CUtensorMap &zmap,
-                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
-                             cudaStream_t st);
-cudaError_t launch_bulk_bf16(int d, const EpochArgs<__nv_bfloat16> &a, const CUtensorMap &zmap,
-                             const CUtensorMap &mmap, int blocks, int warps, int smem_bytes,
-                             cudaStream_t st);
+// `model` selects the instantiation (0 t-distribution, 1 sigmoid).
+cudaError_t launch_bulk_fp32(int d, int model, const EpochArgs<float> &a,
+                             const CUtensorMap &zmap, const CUtensorMap &mmap, int blocks,
+                             int warps, int smem_bytes, cudaStream_t st);
+cudaError_t launch_bulk_bf16(int d, int model, const EpochArgs<__nv_bfloat16> &a,
+                             const CUtensorMap &zmap, const CUtensorMap &mmap, int blocks,
+                             int warps, int smem_bytes, cudaStream_t st);
 
 // Launches the force kernel for one minibatch.  Returns the CUDA error of the
 // launch.  `blocks_cap` bounds the grid (0 = no bound).
