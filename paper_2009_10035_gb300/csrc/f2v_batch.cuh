@@ -31,7 +31,7 @@
 
 namespace f2v {
 
-template <int L, int VEC, typename Ts>
+template <int L, int VEC, typename Ts, int MODEL>
 __global__ void __launch_bounds__(kBatchBlock, 2) force_batch_kernel(const BatchArgs<Ts> a)
 {
     const int lane = threadIdx.x & 31;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) force_batch_kernel(const Batch
         f.err = a.err;
         const FinishCtx fc{r.C, f.slots, f.unit_cnt, nullptr, 0};
         const int item = wu.item0 + grp;
-        if (item < r.n_items) force_item<L, VEC, 1, true, true>(f, fc, item, gl, gmask);
+        if (item < r.n_items) force_item<L, VEC, 1, true, true, MODEL>(f, fc, item, gl, gmask);
         // every store of the unit (rows, tree parts) before the count
         __syncwarp();
         if (lane == 0)
@@ -97,30 +97,38 @@ __global__ void __launch_bounds__(kBatchBlock, 2) force_batch_kernel(const Batch
     }
 }
 
-template <typename Ts>
-const void *batch_kernel_ptr(int shape)
+template <typename Ts, int MODEL>
+const void *batch_kernel_ptr_m(int shape)
 {
     switch (shape) {
-        case 0: return (const void *)force_batch_kernel<1, 2, Ts>;
-        case 1: return (const void *)force_batch_kernel<1, 4, Ts>;
-        case 2: return (const void *)force_batch_kernel<2, 2, Ts>;
-        case 3: return (const void *)force_batch_kernel<2, 4, Ts>;
-        case 4: return (const void *)force_batch_kernel<4, 2, Ts>;
-        case 5: return (const void *)force_batch_kernel<4, 4, Ts>;
-        case 6: return (const void *)force_batch_kernel<8, 2, Ts>;
-        case 7: return (const void *)force_batch_kernel<8, 4, Ts>;
-        case 8: return (const void *)force_batch_kernel<16, 2, Ts>;
-        case 9: return (const void *)force_batch_kernel<16, 4, Ts>;
-        case 10: return (const void *)force_batch_kernel<32, 2, Ts>;
-        case 11: return (const void *)force_batch_kernel<32, 4, Ts>;
+        case 0: return (const void *)force_batch_kernel<1, 2, Ts, MODEL>;
+        case 1: return (const void *)force_batch_kernel<1, 4, Ts, MODEL>;
+        case 2: return (const void *)force_batch_kernel<2, 2, Ts, MODEL>;
+        case 3: return (const void *)force_batch_kernel<2, 4, Ts, MODEL>;
+        case 4: return (const void *)force_batch_kernel<4, 2, Ts, MODEL>;
+        case 5: return (const void *)force_batch_kernel<4, 4, Ts, MODEL>;
+        case 6: return (const void *)force_batch_kernel<8, 2, Ts, MODEL>;
+        case 7: return (const void *)force_batch_kernel<8, 4, Ts, MODEL>;
+        case 8: return (const void *)force_batch_kernel<16, 2, Ts, MODEL>;
+        case 9: return (const void *)force_batch_kernel<16, 4, Ts, MODEL>;
+        case 10: return (const void *)force_batch_kernel<32, 2, Ts, MODEL>;
+        case 11: return (const void *)force_batch_kernel<32, 4, Ts, MODEL>;
         default: return nullptr;
     }
+}
+
+// The kernel of a shape and force model (one instantiation per model, so
+// the model's branches leave the inner loops).
+template <typename Ts>
+const void *batch_kernel_ptr(int shape, int model)
+{
+    return model == 0 ? batch_kernel_ptr_m<Ts, 0>(shape) : batch_kernel_ptr_m<Ts, 1>(shape);
 }
 
 template <typename Ts>
 cudaError_t launch_batch_t(int shape, const BatchArgs<Ts> &a, int blocks, cudaStream_t st)
 {
-    const void *fn = batch_kernel_ptr<Ts>(shape);
+    const void *fn = batch_kernel_ptr<Ts>(shape, a.model);
     if (!fn) return cudaErrorInvalidValue;
     void *args[] = {const_cast<BatchArgs<Ts> *>(&a)};
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBatchBlock), args, 0, st);
@@ -129,12 +137,16 @@ cudaError_t launch_batch_t(int shape, const BatchArgs<Ts> &a, int blocks, cudaSt
 template <typename Ts>
 int batch_resident_t(int shape)
 {
-    const void *fn = batch_kernel_ptr<Ts>(shape);
-    int blocks = 0;
-    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kBatchBlock, 0) !=
-                   cudaSuccess)
-        return 0;
-    return blocks;
+    int best = -1;
+    for (int model = 0; model < 2; ++model) {
+        const void *fn = batch_kernel_ptr<Ts>(shape, model);
+        int blocks = 0;
+        if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kBatchBlock, 0) !=
+                       cudaSuccess)
+            return 0;
+        best = (best < 0) ? blocks : (blocks < best ? blocks : best);
+    }
+    return best;
 }
 
 }  // namespace f2v

@@ -258,13 +258,14 @@ __device__ __forceinline__ void load_partner(const ForceArgs<Ts> &a, int v, int 
 
 // One item (C consecutive pairs of the minibatch) walked by a group of L
 // lanes: lane gl of the group, gmask the group's lanes.
-template <int L, int VEC, int NV, bool EXACT, bool COHERENT, typename Ts>
+template <int L, int VEC, int NV, bool EXACT, bool COHERENT, int MODEL = -1, typename Ts>
 __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishCtx &fc, int item,
                                            int gl, unsigned gmask)
 {
     constexpr int E = VEC * NV;
     constexpr int U = ShapeTraits<L, VEC, NV>::U;
-    const bool tdist = (a.model == 0);
+    // the force model: fixed per instantiation when MODEL >= 0
+    const bool tdist = (MODEL >= 0) ? (MODEL == 0) : (a.model == 0);
     const int q_begin = item * a.C;
     const int q_end = min(q_begin + a.C, a.Pk);
     int u = __ldg(&a.item_u0[item]);       // vertex holding pair q_begin
@@ -336,7 +337,8 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
         const int w = (q < q_end) ? __shfl_sync(gmask, pu, r, L) : -1;
         if (w != ucur) {
             // ---- 4. update: the only place a vertex is finished ------
-            finish_vertex<L, VEC, NV, EXACT>(a, fc, gmask, gl, item, ucur, vbeg, vend, zu, g);
+            finish_vertex<L, VEC, NV, EXACT, MODEL>(a, fc, gmask, gl, item, ucur, vbeg, vend, zu,
+                                                    g);
             if (w < 0) break;
             // next vertex: always ucur + 1, its own row already fetched
             ucur = w;
@@ -401,7 +403,7 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
     }
 }
 
-template <int L, int VEC, int NV, bool EXACT, typename Ts>
+template <int L, int VEC, int NV, bool EXACT, int MODEL, typename Ts>
 __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
 {
     constexpr int G = 32 / L;
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(kBlock) force_kernel(const ForceArgs<Ts> a)
     const int ngroups = gridDim.x * warps * G;
     const FinishCtx fc{a.C, a.slots, a.unit_cnt, nullptr, 0};
     for (int item = gid; item < a.n_items; item += ngroups)
-        force_item<L, VEC, NV, EXACT, false>(a, fc, item, gl, gmask);
+        force_item<L, VEC, NV, EXACT, false, MODEL>(a, fc, item, gl, gmask);
 }
 
 template <int L, int VEC, int NV, bool EXACT, typename Ts>
@@ -427,7 +429,10 @@ cudaError_t launch_shape(const ForceArgs<Ts> &a, int blocks_cap, cudaStream_t st
     int64_t blocks = (a.n_items + groups_per_block - 1) / groups_per_block;
     if (blocks_cap > 0 && blocks > blocks_cap) blocks = blocks_cap;
     if (blocks < 1) blocks = 1;
-    force_kernel<L, VEC, NV, EXACT, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    if (a.model == 0)
+        force_kernel<L, VEC, NV, EXACT, 0, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else
+        force_kernel<L, VEC, NV, EXACT, 1, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 
