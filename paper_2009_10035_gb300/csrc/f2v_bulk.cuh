@@ -288,6 +288,11 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
     bool chunk_start = true;
     int ucur = -1, vbeg = 0, vend = 0;
     float zu[EPL], g[EPL];
+    // t model: the sum of c * (z_u - x) is kept as the sum of -c * x plus
+    // z_u times the sum of c (one multiply-add per element instead of a
+    // subtract and a multiply-add); it is folded in before the vertex's
+    // gradient leaves the warp
+    float csum = 0.f;
 #pragma unroll
     for (int e = 0; e < EPL; ++e) { zu[e] = 0.f; g[e] = 0.f; }
 
@@ -476,9 +481,15 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
             const int re = starts ? __ffs(starts) - 1 : tn;
             const int j = vert[rs];
             if (tu + j != ucur) {
-                if (ucur >= 0)
-                    finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg,
-                                                     vend, zu, g);
+                if (ucur >= 0) {
+                    if (tdist) {
+#pragma unroll
+                        for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
+                    }
+                    finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx,
+                                                            ucur, vbeg, vend, zu, g);
+                }
+                csum = 0.f;
                 vbeg = (ucur >= 0) ? vend : first_lo;
                 ucur = tu + j;
                 vend = vends[rs];
@@ -503,8 +514,9 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
                         load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
                     float *acc = (r & 1) ? g2 : g;
                     if (tdist) {
+                        csum += c;
 #pragma unroll
-                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, zu[e] - x[e], acc[e]);
+                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(-c, x[e], acc[e]);
                     } else {
 #pragma unroll
                         for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
@@ -522,9 +534,9 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
                             load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
                         float *acc = (i & 1) ? g2 : g;
                         if (tdist) {
+                            csum += c;
 #pragma unroll
-                            for (int e = 0; e < EPL; ++e)
-                                acc[e] = fmaf(c, zu[e] - x[e], acc[e]);
+                            for (int e = 0; e < EPL; ++e) acc[e] = fmaf(-c, x[e], acc[e]);
                         } else {
 #pragma unroll
                             for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
@@ -537,8 +549,13 @@ __global__ void __launch_bounds__(D <= 64 ? 512 : 320)
         }
         if (last_of_chunk) {
             // the chunk's last vertex, then the chunk counts as done
-            finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur, vbeg, vend, zu,
-                                             g);
+            if (tdist) {
+#pragma unroll
+                for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
+            }
+            csum = 0.f;
+            finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur,
+                                                    vbeg, vend, zu, g);
             ucur = -1;
             __syncwarp();
             if (lane == 0)
