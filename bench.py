@@ -56,9 +56,11 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["single", "batched", "served"], default="single",
+    ap.add_argument("--workload", choices=["single", "batched", "served", "precision"],
+                    default="single",
                     help="single: one R-MAT graph (the headline); batched: 4,096 SBM graphs; "
-                         "served: Poisson job arrivals to the job server")
+                         "served: Poisson job arrivals to the job server; precision: R-MAT "
+                         "scale 23 with BF16 storage")
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
@@ -524,6 +526,127 @@ def run_batched(args, world, rank, local):
 
 
 # --------------------------------------------------------------------------
+# precision workload: BF16 storage at R-MAT scale 23
+# --------------------------------------------------------------------------
+
+def snowball(g, size, seed=5):
+    """`size` vertices reached breadth-first from a random start (a connected,
+    dense sample of the graph)."""
+    rng = np.random.default_rng(seed)
+    seen = np.zeros(g.n, bool)
+    order = []
+    frontier = [int(rng.integers(g.n))]
+    while frontier and len(order) < size:
+        nxt = []
+        for u in frontier:
+            if seen[u]:
+                continue
+            seen[u] = True
+            order.append(u)
+            if len(order) >= size:
+                break
+            nb = g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]]
+            nxt.extend(int(v) for v in nb[~seen[nb]][:64])
+        frontier = nxt
+        if not frontier and len(order) < size:
+            frontier = [int(v) for v in rng.integers(g.n, size=8)]
+    return np.asarray(order[:size], np.int64)
+
+
+def run_precision(args, world, rank, local):
+    import torch
+    import oracle
+    from paper_2009_10035_gb300 import f2v, graphs
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    d, s, b, lr, E = 128, 10, 16384, 0.02, 10
+    t0 = time.perf_counter()
+    g = graphs.rmat(23, 16, seed=1)
+    t_graph = time.perf_counter() - t0
+    res = {}
+    for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
+        ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                          seed=1, precision=prec, stream=stream)
+        ctx.set_schedule(f2v.LR_LINEAR, E)
+        P = ctx.pairs_per_epoch
+        for _ in range(args.warmup):
+            ctx.epoch()
+        ctx.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        launches0 = ctx.launch_count
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                ctx.epoch()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        ctx.set_kernel_timing(True)
+        ctx.read_kernel_timing()
+        for _ in range(3):
+            ctx.epoch()
+        ctx.synchronize()
+        n_timed, kernel_ms = ctx.read_kernel_timing()
+        ctx.set_kernel_timing(False)
+        res[name] = {"ms_per_step": ms / args.steps, "P": P, "kernel_ms": kernel_ms / max(n_timed, 1),
+                     "launches": ctx.launch_count - launches0, "clocks": clk.summary()}
+        ctx.close()
+    # error against the FP64 oracle on a 10,000-vertex snowball sample
+    sub = graphs.induced_subgraph(g, snowball(g, 10000))
+    Z0 = oracle.init_embedding(sub.n, d, 1)
+    err = {}
+    for ep in (1, E):
+        want = oracle.train(model, sub.row_ptr, sub.col_idx, Z0, s, b, 1, lr, ep,
+                            schedule=1, total_epochs=E)
+        for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
+            with f2v.Context(sub.row_ptr, sub.col_idx, sub.n, d, model=model, s=s, lr=lr,
+                             minibatch=b, seed=1, precision=prec) as c2:
+                c2.set_schedule(f2v.LR_LINEAR, E)
+                c2.train(ep)
+                got = c2.embedding().astype(np.float64)
+            rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-3)
+            err[f"{name}_epochs{ep}"] = {"max_rel": float(rel.max()),
+                                         "median_rel": float(np.median(rel)),
+                                         "rms_abs": float(np.sqrt(np.mean((got - want) ** 2)))}
+    peak, peak_kind = hbm_peak()
+    bf = res["bf16"]
+    alg = bf["P"] * d * 2
+    if rank == 0:
+        line = {
+            "metric": "force-pair updates/s", "value": world * bf["P"] / (bf["ms_per_step"] / 1e3),
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": bf["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "force2vec-precision rmat-scale23 d128 s10 b16384 bf16",
+                       "graph": "R-MAT n=2^23, 16*2^23 directed edges (a=.57,b=c=.19), "
+                                "symmetrised", "n": int(g.n), "nnz": int(g.nnz), "d": d, "s": s,
+                       "minibatch": b, "force_model": args.model,
+                       "lr": f"0.02 linearly decayed over {E} epochs",
+                       "storage": "Z in BF16 with an FP32 master; FP32 accumulation",
+                       "graph_build_s": t_graph},
+            "roofline": {"bound": "hbm", "achieved": alg / (bf["kernel_ms"] / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": alg / (bf["kernel_ms"] / 1e3) / 1e9 / peak, "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs (STREAM-style copy)",
+                         "kernel": "force_bulk_kernel<128, bf16> (one launch per epoch)",
+                         "per_launch": {"algorithmic_bytes": alg, "unit": "pairs x d x 2 B",
+                                        "avg_duration_us": 1e3 * bf["kernel_ms"]}},
+            "fp32_same_graph": {"value": bf["P"] / (res["fp32"]["ms_per_step"] / 1e3),
+                                "ms_per_step": res["fp32"]["ms_per_step"],
+                                "kernel_ms": res["fp32"]["kernel_ms"]},
+            "error_vs_fp64_oracle": {"sample": "10,000-vertex breadth-first sample of the graph, "
+                                               "both sides run on its induced subgraph",
+                                     **err},
+            "gpu_launches": bf["launches"], "clocks": bf["clocks"], "pairs_per_step": bf["P"],
+        }
+        print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
 # served workload: Poisson arrivals of R-MAT jobs to the job server
 # --------------------------------------------------------------------------
 
@@ -624,13 +747,15 @@ def main():
     args = parse()
     world, rank, local = dist_setup(args)
     from paper_2009_10035_gb300 import graphs
-    if args.workload in ("batched", "served"):
+    if args.workload in ("batched", "served", "precision"):
         if args.impl == "reference":
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable":
                                   "the oracle arm is timed on the single-graph workload"}))
         elif args.workload == "batched":
             run_batched(args, world, rank, local)
+        elif args.workload == "precision":
+            run_precision(args, world, rank, local)
         else:
             run_served(args, world, rank, local)
     else:

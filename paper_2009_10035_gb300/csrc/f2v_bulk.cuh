@@ -247,7 +247,7 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
 }
 
 template <int D, typename Ts, int MODEL>
-__global__ void __launch_bounds__(D <= 64 ? 512 : 320)
+__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 320)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
                       const __grid_constant__ CUtensorMap mmap)
@@ -574,7 +574,9 @@ template <int D, typename Ts>
 int bulk_warps()
 {
     const int w = kBulkSmemBudget / BulkLayout<D, Ts>::BYTES;
-    const int cap = (D <= 64 ? 512 : 320) / 32;       // the kernel's launch bound
+    // the kernel's launch bound: 16 warps where the registers allow (BF16 rows
+    // halve the staging buffers, so d = 128 BF16 fits 16 warps per SM)
+    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 320) / 32;
     return w > cap ? cap : w;
 }
 
