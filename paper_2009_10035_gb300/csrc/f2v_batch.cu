@@ -140,13 +140,13 @@ int default_item_pairs(int d) { return d <= 8 ? 128 : 256; }
 
 // Relative GPU time of one pair in a shape's kernel, used to split the SMs
 // between the concurrent launches of an epoch so that they end together.
-// Measured on the 4,096-graph SBM workload with each row size alone: a
-// one-lane shape (L = 1) pays a whole decode per pair (~75); wider shapes pay
-// a shared decode plus the row (~30 + d).
+// Measured on the 4,096-graph SBM workload with each row size alone (ps per
+// pair on the whole GPU): one-lane shapes (L = 1, eight pairs in flight per
+// lane) ~19; wider shapes a shared decode plus the row, ~30 + d.
 double pair_cost(int shape)
 {
     const BatchShape &s = kBatchShapes[shape];
-    return s.L == 1 ? 75.0 : 30.0 + (double)s.d;
+    return s.L == 1 ? 19.0 : 30.0 + (double)s.d;
 }
 }  // namespace
 

@@ -256,6 +256,99 @@ __device__ __forceinline__ void load_partner(const ForceArgs<Ts> &a, int v, int 
     }
 }
 
+// One item walked by a single lane (rows of d <= 4 elements).  A lane has no
+// partners to share a row with, so instead of one pair per step it takes up
+// to T pairs of the current vertex at once: their partner codes (column
+// indices or Philox draws) and then their rows are all in flight together.
+// The gradient adds the pairs in order, as the group walk does.
+template <int VEC, int NV, bool EXACT, bool COHERENT, int MODEL, typename Ts>
+__device__ __forceinline__ void force_item_lane(const ForceArgs<Ts> &a, const FinishCtx &fc,
+                                                int item, unsigned gmask)
+{
+    constexpr int E = VEC * NV;
+    constexpr int T = 8;
+    const bool tdist = (MODEL >= 0) ? (MODEL == 0) : (a.model == 0);
+    const int q_begin = item * a.C;
+    const int q_end = min(q_begin + a.C, a.Pk);
+    int u = __ldg(&a.item_u0[item]);
+    float zu[E], g[E];
+    load_own_row<1, VEC, NV, EXACT>(a, u, 0, zu);
+#pragma unroll
+    for (int e = 0; e < E; ++e) g[e] = 0.f;
+    int vbeg = (int)(__ldg(&a.apair[u]) - a.P0);
+    int vend = (int)(__ldg(&a.apair[u + 1]) - a.P0);
+    int rp_lo = __ldg(&a.row_ptr[u]);
+    int deg = __ldg(&a.row_ptr[u + 1]) - rp_lo;
+    int q = q_begin;
+    while (true) {
+        // pairs q .. q + n - 1, all of vertex u
+        const int n = min(T, min(vend, q_end) - q);
+        int nb[T], kd[T];
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            nb[i] = u;
+            kd[i] = KIND_NONE;
+            if (i < n) {
+                const int j = q + i - vbeg;
+                if (j < deg) {
+                    nb[i] = __ldg(&a.col_idx[rp_lo + j]);
+                    kd[i] = KIND_ATTR;
+                } else if (j - deg < a.s) {
+                    const uint32_t x0 = philox_x0((uint32_t)u, a.epoch, (uint32_t)(j - deg), 0u,
+                                                  a.key0, a.key1);
+                    nb[i] = (int)(x0 % (uint32_t)a.n);
+                    kd[i] = (nb[i] == u) ? KIND_NONE : KIND_REP;
+                }
+            }
+        }
+        float zv[T][E];
+#pragma unroll
+        for (int i = 0; i < T; ++i)
+            if (kd[i] != KIND_NONE) load_partner<1, VEC, NV, EXACT, COHERENT>(a, nb[i], 0, zv[i]);
+#pragma unroll
+        for (int i = 0; i < T; ++i) {
+            if (kd[i] == KIND_NONE) continue;
+            float part = 0.f;
+            if (tdist) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float df = zu[e] - zv[i][e];
+                    part = fmaf(df, df, part);
+                }
+                float coef;
+                if (kd[i] == KIND_ATTR) {
+                    coef = 2.f / (1.f + part);                 // Eq. 8 / t
+                } else {
+                    const float q2 = fmaxf(part, kT2Floor);
+                    coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
+                const float coef = (kd[i] == KIND_ATTR) ? -1.f / (1.f + expf(part))    // Eq. 5
+                                                        : 1.f / (1.f + expf(-part));   // Eq. 6
+#pragma unroll
+                for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
+            }
+        }
+        q += n;
+        if (q < vend && q < q_end) continue;
+        // the vertex's pairs in this item end here
+        finish_vertex<1, VEC, NV, EXACT, MODEL>(a, fc, gmask, 0, item, u, vbeg, vend, zu, g);
+        if (q >= q_end) break;
+        ++u;
+        load_own_row<1, VEC, NV, EXACT>(a, u, 0, zu);
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = 0.f;
+        vbeg = vend;
+        vend = (int)(__ldg(&a.apair[u + 1]) - a.P0);
+        rp_lo = __ldg(&a.row_ptr[u]);
+        deg = __ldg(&a.row_ptr[u + 1]) - rp_lo;
+    }
+}
+
 // One item (C consecutive pairs of the minibatch) walked by a group of L
 // lanes: lane gl of the group, gmask the group's lanes.
 template <int L, int VEC, int NV, bool EXACT, bool COHERENT, int MODEL = -1, typename Ts>
@@ -264,6 +357,10 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
 {
     constexpr int E = VEC * NV;
     constexpr int U = ShapeTraits<L, VEC, NV>::U;
+    if constexpr (L == 1) {
+        force_item_lane<VEC, NV, EXACT, COHERENT, MODEL>(a, fc, item, gmask);
+        return;
+    }
     // the force model: fixed per instantiation when MODEL >= 0
     const bool tdist = (MODEL >= 0) ? (MODEL == 0) : (a.model == 0);
     const int q_begin = item * a.C;
