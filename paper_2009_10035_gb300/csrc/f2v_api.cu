@@ -149,8 +149,13 @@ struct f2v_ctx {
     int32_t *mb_done = nullptr;            // M: chunks finished in this launch
     CUtensorMap zmap{};                    // both Z buffers: 2n rows of the storage type
     CUtensorMap mmap{};                    // the FP32 master (BF16 form)
-    int32_t *partner = nullptr;            // partner code of every pair of an epoch
-    int partner_epoch = -1;                // epoch whose partners `partner` holds
+    // partner codes of every pair of an epoch: two buffers, epoch e in e & 1,
+    // so the next epoch's list is written (on xstream) while this one runs
+    int32_t *partner_buf[2] = {nullptr, nullptr};
+    int partner_epoch[2] = {-1, -1};       // epoch whose partners each buffer holds
+    cudaStream_t xstream = nullptr;        // the next epoch's partner list
+    cudaEvent_t ev_xdone[2] = {nullptr, nullptr};   // buffer written
+    cudaEvent_t ev_xfree[2] = {nullptr, nullptr};   // buffer's last reader done
     int cur = 0;                           // buffer holding Z as of the epoch's start
     int mb_pos = 0;                        // next minibatch of the current epoch
     size_t device_bytes = 0;
@@ -224,9 +229,16 @@ void release(f2v_ctx *c)
                     c->z[0], c->master};
     for (void *p : bufs)
         if (p) cudaFree(p);
-    void *bulk_bufs[] = {c->d_mb_item_base, c->d_mb_C, c->row_flag, c->mb_done, c->partner};
+    if (c->xstream) cudaStreamSynchronize(c->xstream);
+    void *bulk_bufs[] = {c->d_mb_item_base, c->d_mb_C, c->row_flag, c->mb_done,
+                         c->partner_buf[0], c->partner_buf[1]};
     for (void *p : bulk_bufs)
         if (p) cudaFree(p);
+    for (int i = 0; i < 2; ++i) {
+        if (c->ev_xdone[i]) cudaEventDestroy(c->ev_xdone[i]);
+        if (c->ev_xfree[i]) cudaEventDestroy(c->ev_xfree[i]);
+    }
+    if (c->xstream) cudaStreamDestroy(c->xstream);
     if (c->slots) cudaFree(c->slots);
     if (c->unit_cnt) cudaFree(c->unit_cnt);
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
@@ -436,7 +448,7 @@ template <typename Ts>
 void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochArgs<Ts> &ea)
 {
     fill_args(c, k_begin, eta, ea.f);
-    ea.partner = c->partner;
+    ea.partner = c->partner_buf[c->epoch & 1];
     ea.items = c->item_u0;
     ea.mb_item_base = c->d_mb_item_base;
     ea.mb_C = c->d_mb_C;
@@ -465,15 +477,26 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     const int e = c->epoch;
     const float eta = (float)lr_for_epoch(c, e);
     const int step = c->bulk ? (k_end - k_begin) : 1;
-    if (c->bulk && c->partner_epoch != e) {   // this epoch's partner list
+    const int slot = e & 1;
+    if (c->bulk && c->partner_epoch[slot] != e) {   // this epoch's partner list, now
+        // (after any list still being written ahead into this buffer)
+        F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
         cudaError_t ee = launch_expand_partners(
             c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)e, (uint32_t)c->seed,
-            (uint32_t)(c->seed >> 32), c->partner, c->stream);
+            (uint32_t)(c->seed >> 32), c->partner_buf[slot], c->stream);
         c->launches++;
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
-        c->partner_epoch = e;
+        c->partner_epoch[slot] = e;
+    } else if (c->bulk) {
+        // written ahead on the side stream
+        F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
     }
+    // the other buffer's last reader (epoch e - 1) is done once the work
+    // enqueued so far is: the next epoch's list may overwrite it from here
+    const bool prefetch = c->bulk && k_end == num_minibatches(c) &&
+                          c->partner_epoch[slot ^ 1] != e + 1;
+    if (prefetch) F2V_CUDA(c, cudaEventRecord(c->ev_xfree[slot ^ 1], c->stream));
     if (c->bulk)
         F2V_CUDA(c, cudaMemsetAsync(c->mb_done + k_begin, 0,
                                     sizeof(int32_t) * (size_t)(k_end - k_begin), c->stream));
@@ -525,6 +548,20 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
             c->ev_pending.push_back(e0);
             c->ev_pending.push_back(e1);
         }
+    }
+    if (prefetch) {
+        // the next epoch's partner list, on the side stream, overlapping this
+        // epoch's force launch (it only reads the graph and the epoch number)
+        const int ns = slot ^ 1;
+        F2V_CUDA(c, cudaStreamWaitEvent(c->xstream, c->ev_xfree[ns], 0));
+        cudaError_t ee = launch_expand_partners(
+            c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)(e + 1), (uint32_t)c->seed,
+            (uint32_t)(c->seed >> 32), c->partner_buf[ns], c->xstream);
+        c->launches++;
+        if (ee != cudaSuccess)
+            return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
+        F2V_CUDA(c, cudaEventRecord(c->ev_xdone[ns], c->xstream));
+        c->partner_epoch[ns] = e + 1;
     }
     return F2V_OK;
 }
@@ -696,8 +733,16 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
         if (st == F2V_OK) st = alloc(c, (void **)&c->row_flag, sizeof(int32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * 2 * M);
-        if (st == F2V_OK)
-            st = alloc(c, (void **)&c->partner, sizeof(int32_t) * (size_t)c->h_apair[(size_t)n]);
+        for (int i = 0; i < 2 && st == F2V_OK; ++i)
+            st = alloc(c, (void **)&c->partner_buf[i],
+                       sizeof(int32_t) * (size_t)c->h_apair[(size_t)n]);
+        for (int i = 0; i < 2 && st == F2V_OK; ++i)
+            if (cudaEventCreateWithFlags(&c->ev_xdone[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&c->ev_xfree[i], cudaEventDisableTiming) != cudaSuccess)
+                st = fail(c, F2V_ECUDA, "event creation failed");
+        if (st == F2V_OK &&
+            cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking) != cudaSuccess)
+            st = fail(c, F2V_ECUDA, "stream creation failed");
         std::string merr;
         if (st == F2V_OK &&
             (!make_row_map(&c->zmap, c->z[0], 2 * (int64_t)n, d, precision == F2V_BF16, &merr) ||
