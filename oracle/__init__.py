@@ -16,7 +16,9 @@ Every function cites the passage it follows:
   init_embedding  Sec. III-C "Initialization": random Z, uniform [-0.5, 0.5)
   samples         negative samples, s per vertex (Sec. III-C complexity text)
   grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t)
-  train           Algorithm 1 with the SGD update of Eq. 10
+  walk            Algorithm 3 (GenWalk), the rForce2Vec neighbourhood
+  train           Algorithm 1 with the SGD update of Eq. 10 (walk > 0:
+                  rForce2Vec, N(u) from Algorithm 3)
   loss_vertex     Eq. 2 with Eq. 3 (sigmoid) or Eq. 7 (t)
   scores, auc     held-out-edge link prediction, Mann-Whitney AUC
 """
@@ -83,6 +85,15 @@ def _load():
         lib.orc_grad_minibatch_abs.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp, i64,
                                                i64, i32, u64, i32, vp, vp, vp, vp]
         lib.orc_grad_minibatch_abs.restype = None
+        lib.orc_grad_minibatch_walk_abs.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp,
+                                                    i64, i64, i32, i32, u64, i32, vp, vp, vp,
+                                                    vp]
+        lib.orc_grad_minibatch_walk_abs.restype = None
+        lib.orc_walk.argtypes = [u64, vp, vp, i64, i32, i32, vp]
+        lib.orc_walk.restype = None
+        lib.orc_train_walk.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i32, i64, u64,
+                                       f64, i32, i32, i32, i32, i64, vp, vp]
+        lib.orc_train_walk.restype = ctypes.c_int
         lib.orc_learning_rate.argtypes = [f64, i32, i32, i32]
         lib.orc_learning_rate.restype = f64
         lib.orc_train.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i64, u64,
@@ -158,26 +169,32 @@ def samples(n: int, s: int, epoch: int, seed: int) -> np.ndarray:
     return out
 
 
-def grad_minibatch(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
-                   injected=None) -> np.ndarray:
-    """Algorithm 2 for the vertices [u_begin, u_end); returns (u_end-u_begin) x d."""
+def walk(row_ptr, col_idx, u: int, epoch: int, k: int, seed: int) -> np.ndarray:
+    """Algorithm 3 for vertex u in epoch `epoch`: the k vertices the walk
+    reaches, -1 once it has stopped at a vertex without neighbours."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
-    Z = np.ascontiguousarray(Z, dtype=np.float64)
-    n, d = Z.shape
-    sp, si = _injected(injected)
-    g = np.zeros((u_end - u_begin, d), dtype=np.float64)
-    lib.orc_grad_minibatch(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), u_begin,
-                           u_end, s, seed, epoch, _ptr(sp), _ptr(si), _ptr(g))
-    return g
+    out = np.zeros(max(k, 1), dtype=np.int32)
+    if k > 0:
+        lib.orc_walk(seed, _ptr(row_ptr), _ptr(col_idx), u, epoch, k, _ptr(out))
+    return out[:k]
+
+
+def grad_minibatch(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
+                   injected=None, walk=0) -> np.ndarray:
+    """Algorithm 2 for the vertices [u_begin, u_end); returns (u_end-u_begin) x d.
+    walk > 0: N(u) from Algorithm 3 (rForce2Vec)."""
+    return grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
+                              injected=injected, walk=walk)[0]
 
 
 def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
-                       injected=None, gather=None):
+                       injected=None, gather=None, walk=0):
     """Algorithm 2 for [u_begin, u_end): returns (grad, grad_abs), where
     grad_abs sums the absolute values of the per-pair terms element by
     element (the scale of the rounding error of an FP32 evaluation).  With
-    `gather`, partner rows come from that matrix and only z_u from Z."""
+    `gather`, partner rows come from that matrix and only z_u from Z.
+    walk > 0: N(u) from Algorithm 3 (rForce2Vec)."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -187,9 +204,10 @@ def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoc
     sp, si = _injected(injected)
     g = np.zeros((u_end - u_begin, d), dtype=np.float64)
     ga = np.zeros((u_end - u_begin, d), dtype=np.float64)
-    lib.orc_grad_minibatch_abs(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
-                               None if Zp is None else _ptr(Zp), u_begin, u_end, s, seed,
-                               epoch, _ptr(sp), _ptr(si), _ptr(g), _ptr(ga))
+    lib.orc_grad_minibatch_walk_abs(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
+                                    None if Zp is None else _ptr(Zp), u_begin, u_end, s,
+                                    int(walk), seed, epoch, _ptr(sp), _ptr(si), _ptr(g),
+                                    _ptr(ga))
     return g, ga
 
 
@@ -198,16 +216,18 @@ def learning_rate(lr0: float, schedule: int, total_epochs: int, epoch: int) -> f
 
 
 def train(model, row_ptr, col_idx, Z, s, b, seed, lr, epochs, start_epoch=0,
-          schedule=0, total_epochs=0, max_minibatches=-1, injected=None) -> np.ndarray:
-    """Algorithm 1 from embedding Z (copied); returns the new FP64 embedding."""
+          schedule=0, total_epochs=0, max_minibatches=-1, injected=None,
+          walk=0) -> np.ndarray:
+    """Algorithm 1 from embedding Z (copied); returns the new FP64 embedding.
+    walk > 0: rForce2Vec, N(u) from Algorithm 3 with walks of that length."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.array(Z, dtype=np.float64, order="C", copy=True)
     n, d = Z.shape
     sp, si = _injected(injected)
-    rc = lib.orc_train(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), s, b, seed, lr,
-                       schedule, total_epochs, start_epoch, epochs, max_minibatches,
-                       _ptr(sp), _ptr(si))
+    rc = lib.orc_train_walk(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), s, int(walk),
+                            b, seed, lr, schedule, total_epochs, start_epoch, epochs,
+                            max_minibatches, _ptr(sp), _ptr(si))
     if rc != 0:
         raise MemoryError("oracle train: out of memory")
     return Z

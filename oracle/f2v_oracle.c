@@ -22,6 +22,8 @@
  *   repulsive_grad      t-distribution model Eq. 8 / Eq. 9, each times the
  *                       unit vector of Sec. III-B for the t model.
  *   orc_grad_minibatch  Algorithm 2 (GradMinibatch).
+ *   orc_walk            Algorithm 3 (GenWalk): the random-walk neighbourhood
+ *                       of rForce2Vec (Sec. III-F, "rForce2Vec").
  *   orc_train           Algorithm 1 with the update of Eq. 10.
  *   orc_loss_vertex     Eq. 2 with delta from Eq. 3 (sigmoid) or Eq. 7 (t).
  *   orc_auc             Mann-Whitney AUC of held-out edges (evaluation).
@@ -41,6 +43,16 @@
  *   - t model: t^2 is clamped to at least 1e-8 in the repulsive term only.
  *   - Learning-rate schedule: constant, or eta_e = eta0 * (1 - e/E) for a
  *     linearly decayed run of E epochs.
+ *   - rForce2Vec (Alg. 3): N(u) is the sequence of the k vertices a walk of
+ *     k steps from u reaches, repeats included, one attractive pair each (the
+ *     paper's O(nkd) attractive cost; read as a set, the loop of Alg. 3
+ *     would not end on a component of fewer than k + 1 vertices).  Step i
+ *     (0-based) of the walk from u in epoch e moves from w to
+ *       col_idx[row_ptr[w] + Philox(key, ctr=(u, e, i, 1)).x0 mod deg(w)].
+ *     A step that lands on u adds no force (as a sample equal to u); a walk
+ *     that reaches a vertex without out-neighbours (only in a CSR that is not
+ *     symmetric) stops there; a vertex without neighbours has no walk.  The
+ *     walk's pairs come first, then the s negative samples.
  *   - Sigmoid model: after each update every coordinate of z_u is clamped to
  *     [-4, 4].  The paper is silent on divergence; without a bound, Alg. 1 at
  *     eta = 0.02 with the summed gradients of Alg. 2 diverges on graphs with
@@ -143,6 +155,31 @@ void orc_samples(uint64_t seed, int64_t n, int32_t s, int32_t epoch, int32_t *ou
         for (int32_t k = 0; k < s; ++k)
             out[u * s + k] = (int32_t)orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
                                                  (uint32_t)k, (uint32_t)n);
+}
+
+/*
+ * Algorithm 3 (GenWalk) for vertex u in epoch e: out[i] is the vertex step i
+ * reaches, or -1 once the walk has stopped (no neighbours to move to).
+ */
+void orc_walk(uint64_t seed, const int32_t *row_ptr, const int32_t *col_idx, int64_t u,
+              int32_t epoch, int32_t k, int32_t *out)
+{
+    int64_t w = u;                      /* w <- u */
+    int stopped = 0;
+    for (int32_t i = 0; i < k; ++i) {   /* while |N(u)| < k */
+        out[i] = -1;
+        if (stopped) continue;
+        const int32_t lo = row_ptr[w];
+        const int32_t deg = row_ptr[w + 1] - lo;
+        if (deg == 0) {
+            stopped = 1;
+            continue;
+        }
+        /* w_next <- a random neighbour of w; N(u) <- N(u) + {w_next}; w <- w_next */
+        const uint32_t x = philox_x0(seed, (uint32_t)u, (uint32_t)epoch, (uint32_t)i, 1u);
+        w = col_idx[lo + (int32_t)(x % (uint32_t)deg)];
+        out[i] = (int32_t)w;
+    }
 }
 
 /* ------------------------------------------------------------------ */
@@ -256,12 +293,14 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
  * storage form that keeps partner rows in reduced precision beside a full
  * precision copy of each vertex's own row.
  */
-void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
-                            const int32_t *row_ptr, const int32_t *col_idx,
-                            const double *Z, const double *Zp, int64_t u_begin, int64_t u_end,
-                            int32_t s, uint64_t seed, int32_t epoch,
-                            const int64_t *samp_ptr, const int32_t *samp_idx,
-                            double *grad, double *grad_abs)
+/* walk > 0: N(u) is the walk of Algorithm 3 (rForce2Vec) instead of the
+   neighbours of u. */
+void orc_grad_minibatch_walk_abs(int model, int64_t n, int32_t d,
+                                 const int32_t *row_ptr, const int32_t *col_idx,
+                                 const double *Z, const double *Zp, int64_t u_begin,
+                                 int64_t u_end, int32_t s, int32_t walk, uint64_t seed,
+                                 int32_t epoch, const int64_t *samp_ptr,
+                                 const int32_t *samp_idx, double *grad, double *grad_abs)
 {
     if (Zp == NULL) Zp = Z;
     #pragma omp parallel for schedule(dynamic, 16)
@@ -272,9 +311,18 @@ void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
         memset(ga, 0, sizeof ga);
         memset(gr, 0, sizeof gr);
         if (gabs) memset(gabs, 0, sizeof(double) * (size_t)d);
-        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-            const int32_t v = col_idx[e];
-            attractive_grad(model, zu, Zp + (int64_t)v * d, d, ga, gabs);
+        if (walk > 0) {
+            int32_t nw[walk];
+            orc_walk(seed, row_ptr, col_idx, u, epoch, walk, nw);
+            for (int32_t i = 0; i < walk; ++i) {
+                if (nw[i] < 0 || nw[i] == u) continue;
+                attractive_grad(model, zu, Zp + (int64_t)nw[i] * d, d, ga, gabs);
+            }
+        } else {
+            for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                const int32_t v = col_idx[e];
+                attractive_grad(model, zu, Zp + (int64_t)v * d, d, ga, gabs);
+            }
         }
         if (samp_ptr == NULL) {
             for (int32_t k = 0; k < s; ++k) {
@@ -293,6 +341,17 @@ void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
         double *gu = grad + (u - u_begin) * d;
         for (int32_t j = 0; j < d; ++j) gu[j] = ga[j] + gr[j];
     }
+}
+
+void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
+                            const int32_t *row_ptr, const int32_t *col_idx,
+                            const double *Z, const double *Zp, int64_t u_begin, int64_t u_end,
+                            int32_t s, uint64_t seed, int32_t epoch,
+                            const int64_t *samp_ptr, const int32_t *samp_idx,
+                            double *grad, double *grad_abs)
+{
+    orc_grad_minibatch_walk_abs(model, n, d, row_ptr, col_idx, Z, Zp, u_begin, u_end, s, 0,
+                                seed, epoch, samp_ptr, samp_idx, grad, grad_abs);
 }
 
 void orc_grad_minibatch(int model, int64_t n, int32_t d,
@@ -321,14 +380,15 @@ double orc_learning_rate(double lr0, int32_t schedule, int32_t total_epochs, int
  * Runs epochs [start_epoch, start_epoch + epochs) of Algorithm 1 on Z in
  * place.  max_minibatches < 0 runs every minibatch of each epoch; otherwise
  * only the first max_minibatches of each epoch (used to time a bounded
- * sample of a large epoch).  Returns 0, or -1 if memory ran out.
+ * sample of a large epoch).  walk > 0: rForce2Vec, N(u) from Algorithm 3
+ * (orc_train is walk = 0).  Returns 0, or -1 if memory ran out.
  */
-int orc_train(int model, int64_t n, int32_t d,
-              const int32_t *row_ptr, const int32_t *col_idx,
-              double *Z, int32_t s, int64_t b, uint64_t seed,
-              double lr0, int32_t schedule, int32_t total_epochs,
-              int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
-              const int64_t *samp_ptr, const int32_t *samp_idx)
+int orc_train_walk(int model, int64_t n, int32_t d,
+                   const int32_t *row_ptr, const int32_t *col_idx,
+                   double *Z, int32_t s, int32_t walk, int64_t b, uint64_t seed,
+                   double lr0, int32_t schedule, int32_t total_epochs,
+                   int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
+                   const int64_t *samp_ptr, const int32_t *samp_idx)
 {
     double *grad = (double *)malloc((size_t)b * (size_t)d * sizeof(double));
     if (!grad) return -1;
@@ -339,8 +399,8 @@ int orc_train(int model, int64_t n, int32_t d,
             if (max_minibatches >= 0 && nmb >= max_minibatches) break;
             ++nmb;
             const int64_t u1 = (u0 + b < n) ? u0 + b : n;
-            orc_grad_minibatch(model, n, d, row_ptr, col_idx, Z, u0, u1, s, seed, e,
-                               samp_ptr, samp_idx, grad);
+            orc_grad_minibatch_walk_abs(model, n, d, row_ptr, col_idx, Z, NULL, u0, u1, s, walk,
+                                        seed, e, samp_ptr, samp_idx, grad, NULL);
             for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
                 for (int32_t j = 0; j < d; ++j) {
                     double z = Z[u * d + j] - eta * grad[(u - u0) * d + j];
@@ -354,6 +414,18 @@ int orc_train(int model, int64_t n, int32_t d,
     }
     free(grad);
     return 0;
+}
+
+int orc_train(int model, int64_t n, int32_t d,
+              const int32_t *row_ptr, const int32_t *col_idx,
+              double *Z, int32_t s, int64_t b, uint64_t seed,
+              double lr0, int32_t schedule, int32_t total_epochs,
+              int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
+              const int64_t *samp_ptr, const int32_t *samp_idx)
+{
+    return orc_train_walk(model, n, d, row_ptr, col_idx, Z, s, 0, b, seed, lr0, schedule,
+                          total_epochs, start_epoch, epochs, max_minibatches, samp_ptr,
+                          samp_idx);
 }
 
 /* ------------------------------------------------------------------ */

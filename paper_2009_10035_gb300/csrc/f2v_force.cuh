@@ -350,13 +350,14 @@ __device__ __forceinline__ void force_item_lane(const ForceArgs<Ts> &a, const Fi
 }
 
 // One item (C consecutive pairs of the minibatch) walked by a group of L
-// lanes: lane gl of the group, gmask the group's lanes.
-template <int L, int VEC, int NV, bool EXACT, bool COHERENT, int MODEL = -1, typename Ts>
+// lanes: lane gl of the group, gmask the group's lanes; U partner rows in
+// flight at a time.
+template <int L, int VEC, int NV, bool EXACT, bool COHERENT, int MODEL = -1,
+          int U = ShapeTraits<L, VEC, NV>::U, typename Ts>
 __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishCtx &fc, int item,
                                            int gl, unsigned gmask)
 {
     constexpr int E = VEC * NV;
-    constexpr int U = ShapeTraits<L, VEC, NV>::U;
     if constexpr (L == 1) {
         force_item_lane<VEC, NV, EXACT, COHERENT, MODEL>(a, fc, item, gmask);
         return;
