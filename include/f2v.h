@@ -99,6 +99,26 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
                          uint64_t seed, f2v_precision precision, uint32_t flags,
                          void *stream, f2v_ctx **out);
 
+/*
+ * rForce2Vec (Sec. III-C, Algorithm 3): as f2v_create_ex, but in every epoch
+ * N(u) is formed by a random walk of walk_length steps from u (1 <=
+ * walk_length <= 1024) instead of u's neighbours; the force model, the
+ * negative samples and the update are unchanged.  Step i (0-based) of the
+ * walk from u in epoch e moves from the current vertex w (initially u) to
+ * col_idx[row_ptr[w] + Philox4x32-10(key = seed, ctr = (u, e, i, 1)).x0 mod
+ * deg(w)].  Every step is one attractive pair, repeats included; a step that
+ * lands on u exerts no force (as a negative sample equal to u); a walk that
+ * reaches a vertex without out-neighbours (only possible in a CSR that is
+ * not symmetric) stops, its remaining steps exerting no force.  Vertex u's
+ * pairs are its walk_length steps (none if u has no neighbours), then its s
+ * negative samples, so an epoch has walk_length * |{u : deg(u) > 0}| + n * s
+ * pairs.  Walks are drawn on the device once per epoch, one thread per vertex.
+ */
+f2v_status f2v_create_rw(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                         f2v_model model, int32_t s, int32_t walk_length, float lr,
+                         int32_t minibatch, uint64_t seed, f2v_precision precision,
+                         uint32_t flags, void *stream, f2v_ctx **out);
+
 /* Frees every device and host resource of the context.  NULL is a no-op. */
 void f2v_destroy(f2v_ctx *ctx);
 
@@ -164,7 +184,16 @@ f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
    u < n, k < s (count must equal n*s).  For checking; synchronous. */
 f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count);
 
-/* Force pairs of one epoch: nnz + n*s (Sec. III-C complexity: O(md + nsd)). */
+/* Walks the device draws in epoch `epoch` (contexts made by f2v_create_rw):
+   out[u*walk_length + i] is the vertex step i of u's walk reaches, or -1
+   where the step exerts no force (u has no neighbours, the walk has
+   stopped, or the step lands on u).  count must equal n*walk_length.  The
+   walks come from the same kernel and list the force launches read.  For
+   checking; synchronous. */
+f2v_status f2v_debug_walks(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count);
+
+/* Force pairs of one epoch: nnz + n*s (Sec. III-C complexity: O(md + nsd));
+   rForce2Vec: walk_length * |{u : deg(u) > 0}| + n*s (O(nkd + nsd)). */
 f2v_status f2v_pairs_per_epoch(const f2v_ctx *ctx, int64_t *pairs);
 
 /* Device bytes held by the context. */

@@ -23,7 +23,7 @@
  *                       unit vector of Sec. III-B for the t model.
  *   orc_grad_minibatch  Algorithm 2 (GradMinibatch).
  *   orc_walk            Algorithm 3 (GenWalk): the random-walk neighbourhood
- *                       of rForce2Vec (Sec. III-F, "rForce2Vec").
+ *                       of rForce2Vec (Sec. III-C, its rForce2Vec paragraph).
  *   orc_train           Algorithm 1 with the update of Eq. 10.
  *   orc_loss_vertex     Eq. 2 with delta from Eq. 3 (sigmoid) or Eq. 7 (t).
  *   orc_auc             Mann-Whitney AUC of held-out edges (evaluation).

@@ -111,7 +111,9 @@ cudaError_t eval_auc_device(const float *zf, const __nv_bfloat16 *zb, int d, int
 struct f2v_ctx {
     int device = 0;
     int n = 0, d = 0, ld = 0, s = 0, b = 0;
+    int walk = 0;                          // rForce2Vec walk length (0: neighbours, Alg. 2)
     int64_t nnz = 0;
+    int64_t pairs = 0;                     // force pairs per epoch
     int model = 0;
     f2v_precision precision = F2V_FP32;
     uint64_t seed = 0;
@@ -300,8 +302,12 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
 {
     const int n = c->n;
     c->h_apair.assign((size_t)n + 1, 0);
+    c->pairs = 0;
     for (int u = 0; u < n; ++u) {
-        int64_t cu = (int64_t)(row_ptr[u + 1] - row_ptr[u]) + c->s;
+        // N(u): the neighbours, or a walk of c->walk steps if u has any (Alg. 3)
+        const int64_t deg = row_ptr[u + 1] - row_ptr[u];
+        int64_t cu = (c->walk > 0 ? (deg > 0 ? c->walk : 0) : deg) + c->s;
+        c->pairs += cu;
         if (cu == 0) cu = 1;     // the empty pair: the row is still carried over
         c->h_apair[(size_t)u + 1] = c->h_apair[(size_t)u] + cu;
     }
@@ -397,6 +403,22 @@ f2v_status get_event(f2v_ctx *c, cudaEvent_t *e)
 
 int num_minibatches(const f2v_ctx *c) { return (c->n + c->b - 1) / c->b; }
 
+// The staged kernel reads every pair's partner from an expanded list, and
+// so does the register kernel in the rForce2Vec form (walks are drawn once
+// per epoch into the list).
+bool uses_partner_list(const f2v_ctx *c) { return c->bulk || c->walk > 0; }
+
+cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st)
+{
+    c->launches++;
+    if (c->walk > 0)
+        return launch_expand_walks(c->row_ptr, c->col_idx, c->apair, c->n, c->s, c->walk,
+                                   (uint32_t)epoch, (uint32_t)c->seed,
+                                   (uint32_t)(c->seed >> 32), buf, st);
+    return launch_expand_partners(c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)epoch,
+                                  (uint32_t)c->seed, (uint32_t)(c->seed >> 32), buf, st);
+}
+
 // Reads (and clears) the device error word after the stream has drained.
 // A set word means a bounded device wait ran out: the epoch's result is not
 // valid, and the context is marked failed.
@@ -442,6 +464,7 @@ void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
     a.eta = eta;
     a.model = c->model;
     a.err = c->err_word;
+    a.partner = (c->walk > 0) ? c->partner_buf[c->epoch & 1] : nullptr;
 }
 
 template <typename Ts>
@@ -478,23 +501,21 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     const float eta = (float)lr_for_epoch(c, e);
     const int step = c->bulk ? (k_end - k_begin) : 1;
     const int slot = e & 1;
-    if (c->bulk && c->partner_epoch[slot] != e) {   // this epoch's partner list, now
+    const bool listed = uses_partner_list(c);
+    if (listed && c->partner_epoch[slot] != e) {   // this epoch's partner list, now
         // (after any list still being written ahead into this buffer)
         F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
-        cudaError_t ee = launch_expand_partners(
-            c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)e, (uint32_t)c->seed,
-            (uint32_t)(c->seed >> 32), c->partner_buf[slot], c->stream);
-        c->launches++;
+        cudaError_t ee = launch_partner_list(c, e, c->partner_buf[slot], c->stream);
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
         c->partner_epoch[slot] = e;
-    } else if (c->bulk) {
+    } else if (listed) {
         // written ahead on the side stream
         F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
     }
     // the other buffer's last reader (epoch e - 1) is done once the work
     // enqueued so far is: the next epoch's list may overwrite it from here
-    const bool prefetch = c->bulk && k_end == num_minibatches(c) &&
+    const bool prefetch = listed && k_end == num_minibatches(c) &&
                           c->partner_epoch[slot ^ 1] != e + 1;
     if (prefetch) F2V_CUDA(c, cudaEventRecord(c->ev_xfree[slot ^ 1], c->stream));
     if (c->bulk)
@@ -554,10 +575,7 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
         // epoch's force launch (it only reads the graph and the epoch number)
         const int ns = slot ^ 1;
         F2V_CUDA(c, cudaStreamWaitEvent(c->xstream, c->ev_xfree[ns], 0));
-        cudaError_t ee = launch_expand_partners(
-            c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)(e + 1), (uint32_t)c->seed,
-            (uint32_t)(c->seed >> 32), c->partner_buf[ns], c->xstream);
-        c->launches++;
+        cudaError_t ee = launch_partner_list(c, e + 1, c->partner_buf[ns], c->xstream);
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
         F2V_CUDA(c, cudaEventRecord(c->ev_xdone[ns], c->xstream));
@@ -629,10 +647,14 @@ f2v_status f2v_create(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
                          nullptr, out);
 }
 
-f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
-                         f2v_model model, int32_t s, float lr, int32_t minibatch,
-                         uint64_t seed, f2v_precision precision, uint32_t flags,
-                         void *stream, f2v_ctx **out)
+namespace {
+
+constexpr int kMaxWalk = 1024;     // longest rForce2Vec walk accepted
+
+f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                       f2v_model model, int32_t s, int32_t walk, float lr, int32_t minibatch,
+                       uint64_t seed, f2v_precision precision, uint32_t flags, void *stream,
+                       f2v_ctx **out)
 {
     if (!out) return fail(nullptr, F2V_EINVAL, "out is NULL");
     *out = nullptr;
@@ -655,6 +677,7 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         return fail(nullptr, F2V_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(ce));
     }
     c->n = n; c->d = d; c->ld = d; c->s = s; c->b = minibatch; c->model = (int)model;
+    c->walk = walk;
     c->precision = precision; c->seed = seed; c->lr = lr;
     c->stream = (cudaStream_t)stream;
     c->nnz = row_ptr[n];
@@ -733,6 +756,14 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
         if (st == F2V_OK) st = alloc(c, (void **)&c->row_flag, sizeof(int32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * 2 * M);
+        std::string merr;
+        if (st == F2V_OK &&
+            (!make_row_map(&c->zmap, c->z[0], 2 * (int64_t)n, d, precision == F2V_BF16, &merr) ||
+             (precision == F2V_BF16 &&
+              !make_row_map(&c->mmap, c->master, (int64_t)n, d, false, &merr))))
+            st = fail(c, F2V_ECUDA, "tensor map: %s", merr.c_str());
+    }
+    if (st == F2V_OK && uses_partner_list(c)) {
         for (int i = 0; i < 2 && st == F2V_OK; ++i)
             st = alloc(c, (void **)&c->partner_buf[i],
                        sizeof(int32_t) * (size_t)c->h_apair[(size_t)n]);
@@ -743,12 +774,6 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
         if (st == F2V_OK &&
             cudaStreamCreateWithFlags(&c->xstream, cudaStreamNonBlocking) != cudaSuccess)
             st = fail(c, F2V_ECUDA, "stream creation failed");
-        std::string merr;
-        if (st == F2V_OK &&
-            (!make_row_map(&c->zmap, c->z[0], 2 * (int64_t)n, d, precision == F2V_BF16, &merr) ||
-             (precision == F2V_BF16 &&
-              !make_row_map(&c->mmap, c->master, (int64_t)n, d, false, &merr))))
-            st = fail(c, F2V_ECUDA, "tensor map: %s", merr.c_str());
     }
     if (st != F2V_OK) {
         g_last_error = c->err;
@@ -792,6 +817,30 @@ f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t
 #undef CREATE_CUDA
     *out = c;
     return F2V_OK;
+}
+
+}  // namespace
+
+f2v_status f2v_create_ex(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                         f2v_model model, int32_t s, float lr, int32_t minibatch,
+                         uint64_t seed, f2v_precision precision, uint32_t flags,
+                         void *stream, f2v_ctx **out)
+{
+    return create_impl(row_ptr, col_idx, n, d, model, s, 0, lr, minibatch, seed, precision,
+                       flags, stream, out);
+}
+
+f2v_status f2v_create_rw(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int32_t d,
+                         f2v_model model, int32_t s, int32_t walk_length, float lr,
+                         int32_t minibatch, uint64_t seed, f2v_precision precision,
+                         uint32_t flags, void *stream, f2v_ctx **out)
+{
+    if (out) *out = nullptr;
+    if (walk_length < 1 || walk_length > kMaxWalk)
+        return fail(nullptr, F2V_EINVAL, "walk_length = %d, must be in [1, %d]", walk_length,
+                    kMaxWalk);
+    return create_impl(row_ptr, col_idx, n, d, model, s, walk_length, lr, minibatch, seed,
+                       precision, flags, stream, out);
 }
 
 void f2v_destroy(f2v_ctx *ctx)
@@ -1019,10 +1068,41 @@ f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t c
     return F2V_OK;
 }
 
+f2v_status f2v_debug_walks(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!out) return fail(ctx, F2V_EINVAL, "out is NULL");
+    if (epoch < 0) return fail(ctx, F2V_EINVAL, "epoch < 0");
+    if (ctx->walk < 1) return fail(ctx, F2V_ESTATE, "the context has no walks (f2v_create_rw)");
+    const size_t want = (size_t)ctx->n * (size_t)ctx->walk;
+    if (count != want)
+        return fail(ctx, F2V_EINVAL, "count = %zu, expected n*walk_length = %zu", count, want);
+    DeviceGuard g(ctx->device);
+    const size_t slots = (size_t)ctx->h_apair[(size_t)ctx->n];
+    int32_t *list = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&list, slots * sizeof(int32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dout, want * sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) {
+        if (list) cudaFreeAsync(list, ctx->stream);
+        return fail(ctx, F2V_ENOMEM, "debug_walks: %s", cudaGetErrorString(e));
+    }
+    // the list the epoch's force launches read, written by the same kernel
+    F2V_CUDA(ctx, launch_partner_list(ctx, epoch, list, ctx->stream));
+    F2V_CUDA(ctx, launch_extract_walks(ctx->apair, ctx->row_ptr, ctx->n, ctx->walk, list, dout,
+                                       ctx->stream));
+    ctx->launches++;
+    F2V_CUDA(ctx, cudaMemcpyAsync(out, dout, want * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    F2V_CUDA(ctx, cudaFreeAsync(list, ctx->stream));
+    F2V_CUDA(ctx, cudaFreeAsync(dout, ctx->stream));
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return F2V_OK;
+}
+
 f2v_status f2v_pairs_per_epoch(const f2v_ctx *ctx, int64_t *pairs)
 {
     if (!ctx || !pairs) return fail(nullptr, F2V_EINVAL, "null argument");
-    *pairs = ctx->nnz + (int64_t)ctx->n * ctx->s;
+    *pairs = ctx->pairs;
     return F2V_OK;
 }
 

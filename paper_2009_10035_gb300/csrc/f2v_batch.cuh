@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kBatchBlock, 2) force_batch_kernel(const Batch
         f.col_idx = gr.col_idx;
         f.apair = gr.apair;
         f.item_u0 = a.item_u0 + r.item_off;
+        f.partner = nullptr;
         f.zcur = static_cast<const Ts *>(gr.z[st.cur]);
         f.znext = static_cast<Ts *>(gr.z[st.cur ^ 1]);
         f.master = gr.master;

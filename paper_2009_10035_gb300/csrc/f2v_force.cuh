@@ -10,7 +10,8 @@
 //   1. decode -- lane t finds the vertex and the partner of pair t of the
 //      tile from a window of L consecutive vertices (pair prefix, row
 //      pointers), reading the partner from col_idx (attractive) or drawing it
-//      with Philox (repulsive);
+//      with Philox (repulsive), or, in the rForce2Vec form, reading its code
+//      from the epoch's expanded partner list;
 //   2. gather -- the group fetches the partner rows, U at a time, each lane
 //      a VEC-wide vector of NV slices (128-bit loads for FP32 rows of d >= 4);
 //   3. force -- the dot product (sigmoid) or squared distance (t model) is
@@ -238,6 +239,19 @@ __device__ __forceinline__ void finish_vertex(const ForceArgs<Ts> &a, const Fini
     }
 }
 
+// A pair's partner from its code in an expanded partner list (rForce2Vec);
+// a code without a force leaves nb and kind as they are (kind KIND_NONE).
+__device__ __forceinline__ void decode_code(int code, int &nb, int &kind)
+{
+    if (code >= 0) {
+        nb = code;
+        kind = KIND_ATTR;
+    } else if (code != kPartnerNone) {
+        nb = -2 - code;
+        kind = KIND_REP;
+    }
+}
+
 // Partner row v: from the next buffer if an earlier minibatch of this epoch
 // wrote it, else from the current one.  Rows written earlier in the same
 // launch (COHERENT: the batched kernel) are read through L2 only, since L1 is
@@ -288,7 +302,9 @@ __device__ __forceinline__ void force_item_lane(const ForceArgs<Ts> &a, const Fi
         for (int i = 0; i < T; ++i) {
             nb[i] = u;
             kd[i] = KIND_NONE;
-            if (i < n) {
+            if (i < n && a.partner) {
+                decode_code(__ldg(&a.partner[a.P0 + q + i]), nb[i], kd[i]);
+            } else if (i < n) {
                 const int j = q + i - vbeg;
                 if (j < deg) {
                     nb[i] = __ldg(&a.col_idx[rp_lo + j]);
@@ -409,7 +425,9 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
                 const int prp_hi = __shfl_sync(gmask, rp_hi, off, L);
                 nb = pu;
                 kind = KIND_NONE;
-                if (q + gl < q_end) {
+                if (q + gl < q_end && a.partner) {
+                    decode_code(__ldg(&a.partner[a.P0 + q + gl]), nb, kind);
+                } else if (q + gl < q_end) {
                     const int j = q + gl - pA_lo;
                     const int deg = prp_hi - prp_lo;
                     if (j < deg) {

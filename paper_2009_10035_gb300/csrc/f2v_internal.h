@@ -50,6 +50,8 @@ struct ForceArgs {
     const int32_t *col_idx;    // nnz
     const int64_t *apair;      // n + 1
     const int32_t *item_u0;    // items of this minibatch
+    const int32_t *partner;    // if not null: the epoch's partner codes (pair P0 + q),
+                               // read instead of col_idx and Philox (rForce2Vec)
     const Ts *zcur;            // n x ld
     Ts *znext;                 // n x ld
     float *master;             // BF16 form: FP32 master rows (n x ld); else nullptr
@@ -98,9 +100,10 @@ struct EpochArgs {
 bool make_row_map(CUtensorMap *map, void *base, int64_t rows, int d, bool bf16,
                   std::string *err);
 
-// Partner codes of the expanded pair list: v >= 0 a neighbour (attractive
-// force), -2 - w a negative sample w (repulsive force), -1 no force (a sample
-// that drew u itself, or the empty pair of a vertex with deg + s = 0).
+// Partner codes of the expanded pair list: v >= 0 a neighbour or a vertex a
+// walk reached (attractive force), -2 - w a negative sample w (repulsive
+// force), -1 no force (a sample or walk step that drew u itself, a walk step
+// after the walk stopped, or the empty pair of a vertex without pairs).
 constexpr int32_t kPartnerNone = -1;
 
 // Writes the partner code of every pair of epoch `epoch` (pair apair[u] + j
@@ -109,6 +112,21 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
                                    const int64_t *apair, int32_t n, int32_t s, uint32_t epoch,
                                    uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st);
+
+// rForce2Vec (Algorithm 3): the same list with vertex u's first `walk` pairs
+// (if u has neighbours) the steps of a random walk from u, one thread per
+// vertex: step i moves from w to its neighbour number
+// Philox(key, ctr = (u, epoch, i, 1)).x0 mod deg(w).
+cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
+                                const int64_t *apair, int32_t n, int32_t s, int32_t walk,
+                                uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
+                                cudaStream_t st);
+
+// out[u * walk + i]: the code of walk step i of vertex u in the list
+// `partner` (kPartnerNone for a vertex without neighbours).
+cudaError_t launch_extract_walks(const int64_t *apair, const int32_t *row_ptr, int32_t n,
+                                 int32_t walk, const int32_t *partner, int32_t *out,
+                                 cudaStream_t st);
 
 // Kernel shape chosen from d: a group of L lanes owns one force pair at a
 // time; each lane holds NV vectors of VEC consecutive elements of a row.

@@ -71,6 +71,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         sigs = {
             "f2v_create": ([vp, vp, i32, i32, st, i32, f32, i32, u64, pp], st),
             "f2v_create_ex": ([vp, vp, i32, i32, st, i32, f32, i32, u64, st, u32, vp, pp], st),
+            "f2v_create_rw": ([vp, vp, i32, i32, st, i32, i32, f32, i32, u64, st, u32, vp, pp],
+                              st),
             "f2v_destroy": ([vp], None),
             "f2v_epoch": ([vp], st),
             "f2v_train": ([vp, i32], st),
@@ -87,6 +89,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_set_stream": ([vp, vp], st),
             "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
             "f2v_debug_samples": ([vp, i32, vp, sz], st),
+            "f2v_debug_walks": ([vp, i32, vp, sz], st),
             "f2v_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
             "f2v_device_bytes": ([vp, ctypes.POINTER(sz)], st),
             "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
@@ -154,13 +157,16 @@ def _stream_handle(stream) -> int | None:
 
 
 class Context:
-    """One embedding job: a graph, its device-resident Z and the epoch counter."""
+    """One embedding job: a graph, its device-resident Z and the epoch counter.
+    walk_length > 0 makes it rForce2Vec (f2v_create_rw): N(u) from random
+    walks of that many steps (Algorithm 3) instead of u's neighbours."""
 
     def __init__(self, row_ptr, col_idx, n: int, d: int, model: int = TDIST, s: int = 5,
                  lr: float = 0.02, minibatch: int = 256, seed: int = 1,
-                 precision: int = FP32, flags: int = 0, stream=None):
+                 precision: int = FP32, flags: int = 0, stream=None, walk_length: int = 0):
         self._lib = load_library()
         self.n, self.d, self.s = int(n), int(d), int(s)
+        self.walk_length = int(walk_length)
         self.model, self.precision = int(model), int(precision)
         rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
         ci = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -169,10 +175,16 @@ class Context:
         if ci.size == 0:
             ci = np.zeros(1, dtype=np.int32)
         h = ctypes.c_void_p()
-        rc = self._lib.f2v_create_ex(_ptr(rp), _ptr(ci), self.n, self.d, int(model), self.s,
-                                     float(lr), int(minibatch), int(seed) & (2**64 - 1),
-                                     int(precision), int(flags), _stream_handle(stream),
-                                     ctypes.byref(h))
+        if self.walk_length:
+            rc = self._lib.f2v_create_rw(_ptr(rp), _ptr(ci), self.n, self.d, int(model), self.s,
+                                         self.walk_length, float(lr), int(minibatch),
+                                         int(seed) & (2**64 - 1), int(precision), int(flags),
+                                         _stream_handle(stream), ctypes.byref(h))
+        else:
+            rc = self._lib.f2v_create_ex(_ptr(rp), _ptr(ci), self.n, self.d, int(model), self.s,
+                                         float(lr), int(minibatch), int(seed) & (2**64 - 1),
+                                         int(precision), int(flags), _stream_handle(stream),
+                                         ctypes.byref(h))
         if rc != OK:
             raise F2VError(rc, self._lib.f2v_last_error_global().decode())
         self._h = h
@@ -268,6 +280,14 @@ class Context:
         out = np.zeros((self.n, self.s), dtype=np.int32)
         buf = out if out.size else np.zeros(1, np.int32)
         self._check(self._lib.f2v_debug_samples(self._h, int(epoch), _ptr(buf), out.size))
+        return out
+
+    def debug_walks(self, epoch: int) -> np.ndarray:
+        """n x walk_length: the vertex each walk step reaches, -1 where the
+        step exerts no force."""
+        out = np.zeros((self.n, self.walk_length), dtype=np.int32)
+        buf = out if out.size else np.zeros(1, np.int32)
+        self._check(self._lib.f2v_debug_walks(self._h, int(epoch), _ptr(buf), out.size))
         return out
 
     @property

@@ -69,7 +69,7 @@ def bf16_round(x):
 
 
 def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedule=None,
-                total_epochs=0, precision=f2v.FP32, tol=TOL_STEP, flags=0):
+                total_epochs=0, precision=f2v.FP32, tol=TOL_STEP, flags=0, walk=0):
     """Minibatch by minibatch: the oracle computes each checked minibatch's
     update (Algorithm 2 + Eq. 10) from the GPU's own Z before it, so that each
     kernel launch is compared in isolation.  Error bound: FP32 accumulation of
@@ -78,7 +78,7 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
     M = -(-g.n // b)
     worst = 0.0
     with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
-                     seed=seed, precision=precision, flags=flags) as ctx:
+                     seed=seed, precision=precision, flags=flags, walk_length=walk) as ctx:
         if schedule is not None:
             ctx.set_schedule(schedule, total_epochs)
         for e in range(epochs):
@@ -93,7 +93,7 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
                 u0, u1 = k * b, min(g.n, (k + 1) * b)
                 gather = bf16_round(before) if precision == f2v.BF16 else None
                 G, A = oracle.grad_minibatch_abs(model, g.row_ptr, g.col_idx, before, u0, u1,
-                                                 s, seed, e, gather=gather)
+                                                 s, seed, e, gather=gather, walk=walk)
                 eta = oracle.learning_rate(lr, 0 if schedule is None else schedule,
                                            total_epochs, e)
                 want = before[u0:u1] - eta * G
@@ -379,3 +379,111 @@ def test_rmat_scale20_auc_after_20_epochs(model, rmat20):
     auc_oracle = oracle.link_auc(model, Zo, g.test_pos, g.test_neg)
     print(f"AUC model={model}: gpu {auc_gpu:.5f} oracle {auc_oracle:.5f}")
     assert abs(auc_gpu - auc_oracle) <= 0.005
+
+
+# ---------------------------------------------------------------- rForce2Vec (Algorithm 3)
+
+def oracle_walks(g, k, epoch, seed):
+    """The walks as f2v_debug_walks reports them: a step that lands on u
+    exerts no force and reads -1."""
+    W = np.array([oracle.walk(g.row_ptr, g.col_idx, u, epoch, k, seed) for u in range(g.n)],
+                 dtype=np.int32).reshape(g.n, k)
+    W[W == np.arange(g.n, dtype=np.int32)[:, None]] = -1
+    return W
+
+
+@pytest.mark.parametrize("epoch", [0, 3])
+@pytest.mark.parametrize("k", [1, 5])
+def test_walks_bit_exact(epoch, k):
+    # avg degree ~4: isolated vertices (no walk), leaves (walks that return)
+    g = graphs.erdos_renyi(3000, p=0.0013, seed=5)
+    assert (g.degrees() == 0).any()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, s=3, minibatch=512, seed=21,
+                     walk_length=k) as ctx:
+        got = ctx.debug_walks(epoch)
+        assert ctx.pairs_per_epoch == k * int((g.degrees() > 0).sum()) + g.n * 3
+    np.testing.assert_array_equal(got, oracle_walks(g, k, epoch, 21))
+
+
+def test_walks_stop_at_a_dead_end():
+    # a CSR that is not symmetric: 0 -> 1 -> 2 -> 3, and 3 has no out-neighbours
+    n = 6
+    rp = np.array([0, 1, 2, 3, 3, 4, 5], np.int32)
+    ci = np.array([1, 2, 3, 5, 4], np.int32)
+    g = graphs.Graph(n=n, row_ptr=rp, col_idx=ci, name="chain")
+    with f2v.Context(rp, ci, n, 4, s=1, minibatch=4, seed=3, walk_length=5) as ctx:
+        got = ctx.debug_walks(1)
+    assert got[0].tolist() == [1, 2, 3, -1, -1]
+    assert got[3].tolist() == [-1] * 5
+    np.testing.assert_array_equal(got, oracle_walks(g, 5, 1, 3))
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [4, 8, 32, 128])
+def test_walk_steps(model, d):
+    """rForce2Vec, one launch at a time against Algorithm 2 on the oracle's
+    walks: the register kernel (d = 4, 8, 32) and the staged kernel (128)."""
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, d, model, 4, 256, lr=0.05, seed=4, epochs=2, walk=5,
+                steps={(0, 0), (0, 3), (1, 2), (1, 5)})
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_walk_register_kernel_where_staged_exists(model):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, 128, model, 4, 256, lr=0.05, seed=4, epochs=1, walk=5,
+                steps={(0, 0), (0, 4)}, flags=f2v.FLAG_NO_STAGING)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_walk_bf16_steps(model):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, 128, model, 4, 256, lr=0.05, seed=4, epochs=1, walk=5,
+                steps={(0, 1), (0, 5)}, precision=f2v.BF16)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_walk_whole_epochs(model):
+    """Two whole epochs (walks of the next epoch drawn ahead on the side
+    stream) against the oracle's Algorithm 1 with walks, element by element."""
+    g = graphs.erdos_renyi(1000, p=0.006, seed=9)
+    for d in (32, 128):
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=5, lr=0.02, minibatch=128,
+                         seed=6, walk_length=5) as ctx:
+            ctx.train(2)
+            got = ctx.embedding()
+        Z0 = oracle.init_embedding(g.n, d, 6)
+        want = oracle.train(model, g.row_ptr, g.col_idx, Z0, 5, 128, 6, 0.02, 2, walk=5)
+        err = rel_err(got, want)
+        assert err.max() <= 1e-4, (d, float(err.max()))
+
+
+def test_walk_runs_are_bit_reproducible():
+    g = graphs.erdos_renyi(2000, p=0.004, seed=10)
+    outs = []
+    for _ in range(2):
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, s=5, minibatch=256, seed=2,
+                         walk_length=5) as ctx:
+            ctx.train(2)
+            outs.append(ctx.embedding())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_walk_length_is_validated():
+    g = graphs.erdos_renyi(100, p=0.05, seed=1)
+    for k in (-1, 1025):
+        with pytest.raises(f2v.F2VError):
+            f2v.Context(g.row_ptr, g.col_idx, g.n, 8, walk_length=k)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_rmat_scale20_d128_walk_steps(model, rmat20):
+    """rForce2Vec on the benchmark graph and launch configuration (walk
+    length 5, as the paper's rForce2Vec runs), sampled launches."""
+    g = rmat20
+    b = 4096
+    M = -(-g.n // b)
+    steps = {(0, 0), (0, M // 2 + 1), (0, M - 1)}
+    worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps, walk=5,
+                        schedule=f2v.LR_LINEAR, total_epochs=20)
+    print(f"rmat20 walks model={model}: worst scaled error {worst:.3e}")
