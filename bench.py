@@ -11,6 +11,10 @@ Metric: force-pair updates per second, pairs = nnz + n*s per epoch.
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
 oracle on a bounded sample of the same workload instead.
 
+`--walk K` makes the single-graph workload rForce2Vec (Algorithm 3: N(u)
+from a K-step random walk per vertex and epoch; the paper's runs use K = 5
+with the sigmoid model); pairs = K * (vertices with neighbours) + n*s.
+
 `--workload batched` times the batched form instead: 4,096 SBM graphs (n
 log-uniform in [50, 20000], 2-16 equal blocks, p_in 0.05, p_out 0.002), d
 round-robin 2 / 16 / 64 FP32, s = 5, minibatch 128, lr 0.02 linearly decayed
@@ -52,6 +56,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=20)
     ap.add_argument("--model", choices=["tdist", "sigmoid"], default="tdist")
+    ap.add_argument("--walk", type=int, default=0,
+                    help="rForce2Vec walk length (0: 1-hop neighbourhoods)")
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
@@ -85,12 +91,15 @@ def hbm_peak():
 
 
 def workload_config(g, args, d=128, s=5, b=4096):
+    walk = f" rwalk{args.walk}" if args.walk else ""
     return {
-        "workload": f"force2vec-epoch rmat-scale{args.scale} holdout5% d{d} s{s} b{b}",
+        "workload": f"force2vec-epoch rmat-scale{args.scale} holdout5% d{d} s{s} b{b}{walk}",
         "graph": f"R-MAT n=2^{args.scale}, 16*2^{args.scale} directed edges (a=.57,b=c=.19), "
                  "symmetrised, 5% undirected edges held out",
         "n": int(g.n), "nnz": int(g.nnz), "d": d, "s": s, "minibatch": b,
         "force_model": args.model, "lr": "0.02 linearly decayed",
+        "neighbourhood": (f"random walks of {args.walk} steps (Algorithm 3)" if args.walk
+                          else "1-hop neighbours (Algorithm 2)"),
         "step": "one epoch (all minibatches)",
         "l2": "inputs larger than L2 (Z 2 x 512 MB FP32 double buffer, CSR 120 MB; L2 129 MB)",
     }
@@ -177,25 +186,33 @@ def max_over_ranks(x: float, world: int) -> float:
 # CPU oracle (baseline leg and the reference arm)
 # --------------------------------------------------------------------------
 
-def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None):
+def vertex_pairs(g, s, walk):
+    """Force pairs of each vertex per epoch: its neighbours (or walk steps,
+    if it has neighbours) and its s samples."""
+    deg = g.degrees().astype(np.int64)
+    return (np.where(deg > 0, walk, 0) if walk else deg) + s
+
+
+def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None, walk=0):
     """Times the FP64 oracle over the first minibatches of epoch 0 until about
     `budget_s` seconds of work; returns (pairs/s, pairs, minibatches, threads)."""
     import oracle
     threads = oracle.set_threads(0)
     Z = oracle.init_embedding(g.n, d, seed)
-    deg = g.degrees()
+    vp = vertex_pairs(g, s, walk)
     M = -(-g.n // b)
     done_mb, pairs, elapsed = 0, 0, 0.0
     chunk = 4
     while done_mb < M and elapsed < budget_s and (max_mb is None or done_mb < max_mb):
         k1 = min(M, done_mb + chunk)
         u0, u1 = done_mb * b, min(g.n, k1 * b)
-        sub_pairs = int(deg[u0:u1].sum()) + (u1 - u0) * s
+        sub_pairs = int(vp[u0:u1].sum())
         t0 = time.perf_counter()
         # run minibatches [done_mb, k1) of epoch 0 on the current Z
         for k in range(done_mb, k1):
             a0, a1 = k * b, min(g.n, (k + 1) * b)
-            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0)
+            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0,
+                                      walk=walk)
             Z[a0:a1] -= 0.02 * G
         elapsed += time.perf_counter() - t0
         pairs += sub_pairs
@@ -211,7 +228,7 @@ def run_reference(args, g, world, rank):
     threads = oracle.set_threads(0)
     d, s, b, seed = 128, 5, 4096, 1
     Z = oracle.init_embedding(g.n, d, seed)
-    deg = g.degrees()
+    vp = vertex_pairs(g, s, args.walk)
     mb_per_step = 4
     M = -(-g.n // b)
 
@@ -220,9 +237,10 @@ def run_reference(args, g, world, rank):
         pairs = 0
         for k in range(k0, min(M, k0 + mb_per_step)):
             a0, a1 = k * b, min(g.n, (k + 1) * b)
-            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0)
+            G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0,
+                                      walk=args.walk)
             Z[a0:a1] -= 0.02 * G
-            pairs += int(deg[a0:a1].sum()) + (a1 - a0) * s
+            pairs += int(vp[a0:a1].sum())
         return pairs
 
     for i in range(args.warmup):
@@ -265,7 +283,7 @@ def run_ours(args, g, world, rank, local):
 
     def make(m):
         ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=m, s=s, lr=lr, minibatch=b,
-                          seed=seed, stream=stream)
+                          seed=seed, stream=stream, walk_length=args.walk)
         ctx.set_schedule(f2v.LR_LINEAR, total_epochs)
         return ctx
 
@@ -308,7 +326,8 @@ def run_ours(args, g, world, rank, local):
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        if tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.scale:
+        if (tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.scale
+                and not args.walk):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -355,7 +374,7 @@ def run_ours(args, g, world, rank, local):
 
         def job():
             with f2v.Context(rp.numpy(), ci.numpy(), g.n, d, model=model, s=s, lr=lr,
-                             minibatch=b, seed=seed, stream=stream) as c:
+                             minibatch=b, seed=seed, stream=stream, walk_length=args.walk) as c:
                 c.set_schedule(f2v.LR_LINEAR, job_epochs)
                 c.train(job_epochs)
                 c.embedding_into_host(zout.numpy())
@@ -376,7 +395,7 @@ def run_ours(args, g, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds)
+        rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds, walk=args.walk)
         cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "kind": "oracle",
                "sample": f"first {mbs} minibatches (b=4096) of epoch 0, {pairs} pairs, FP64, "
                          f"{el:.1f} s"}
