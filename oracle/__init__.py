@@ -15,7 +15,8 @@ Every function cites the passage it follows:
                   generator both sides implement from its published definition
   init_embedding  Sec. III-C "Initialization": random Z, uniform [-0.5, 0.5)
   samples         negative samples, s per vertex (Sec. III-C complexity text)
-  grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t)
+  grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t),
+                  Table "diffmodels" (FR, LinLog, ForceAtlas)
   walk            Algorithm 3 (GenWalk), the rForce2Vec neighbourhood
   train           Algorithm 1 with the SGD update of Eq. 10 (walk > 0:
                   rForce2Vec, N(u) from Algorithm 3)
@@ -33,6 +34,9 @@ import numpy as np
 
 TDIST = 0
 SIGMOID = 1
+FR = 2            # Fruchterman-Reingold (Table "diffmodels")
+LINLOG = 3
+FORCEATLAS = 4
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "f2v_oracle.c")

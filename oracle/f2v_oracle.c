@@ -20,7 +20,10 @@
  *                       in the complexity paragraph of Sec. III-C).
  *   attractive_grad,    per-pair gradients: sigmoid model Eq. 5 / Eq. 6,
  *   repulsive_grad      t-distribution model Eq. 8 / Eq. 9, each times the
- *                       unit vector of Sec. III-B for the t model.
+ *                       unit vector of Sec. III-B for the t model; the
+ *                       Fruchterman-Reingold, LinLog and ForceAtlas models
+ *                       of Table "diffmodels" (Sec. III-A, "Other
+ *                       force-directed models"), also along the unit vector.
  *   orc_grad_minibatch  Algorithm 2 (GradMinibatch).
  *   orc_walk            Algorithm 3 (GenWalk): the random-walk neighbourhood
  *                       of rForce2Vec (Sec. III-C, its rForce2Vec paragraph).
@@ -53,7 +56,22 @@
  *     that reaches a vertex without out-neighbours (only in a CSR that is not
  *     symmetric) stops there; a vertex without neighbours has no walk.  The
  *     walk's pairs come first, then the s negative samples.
- *   - Sigmoid model: after each update every coordinate of z_u is clamped to
+ *   - Table "diffmodels" (FR, LinLog, ForceAtlas) lists each model's force
+ *     on u along the unit vector (z_u - z_x)/t, t = |z_u - z_x|: negative
+ *     for the attraction toward a neighbour, positive for the repulsion
+ *     from a sample.  Eq. 10 steps against the gradient, so the per-pair
+ *     gradient is minus that force times the unit vector:
+ *       FR         attractive  t^2 (z_u - z_v)/t = t (z_u - z_v)
+ *       LinLog     attractive  log(1 + t) (z_u - z_v)/t
+ *       ForceAtlas attractive  (z_u - z_v)
+ *       all three  repulsive   -(1/t) (z_u - z_w)/t = -(z_u - z_w)/t^2,
+ *     with t^2 floored at 1e-8 as in the t model.  (Read as gradients, the
+ *     listed signs would push neighbours apart and pull samples together.)
+ *     Their forces grow (FR, LinLog, ForceAtlas attraction) or stay finite
+ *     with distance, so like the sigmoid model they take the coordinate
+ *     bound below.
+ *   - Sigmoid (and FR, LinLog, ForceAtlas) models: after each update every
+ *     coordinate of z_u is clamped to
  *     [-4, 4].  The paper is silent on divergence; without a bound, Alg. 1 at
  *     eta = 0.02 with the summed gradients of Alg. 2 diverges on graphs with
  *     high-degree vertices even in FP64 (max |z| grows ~1e5-fold per epoch on
@@ -69,6 +87,9 @@
 
 #define ORC_TDIST 0
 #define ORC_SIGMOID 1
+#define ORC_FR 2           /* Fruchterman-Reingold (Table "diffmodels") */
+#define ORC_LINLOG 3
+#define ORC_FORCEATLAS 4
 
 #define ORC_T2_FLOOR 1e-8
 #define ORC_SIGMOID_BOUND 4.0
@@ -236,6 +257,30 @@ static void attractive_grad(int model, const double *zu, const double *zv, int32
         const double c = -(1.0 - sigma(x));
         for (int32_t j = 0; j < d; ++j) g[j] += c * zv[j];
         if (gabs) add_scale(gabs, zv, d, c, sigma(x) * (1.0 - sigma(x)), dot_abs(zu, zv, d));
+    } else if (model != ORC_TDIST) {
+        /* Table "diffmodels": minus the listed force times the unit vector */
+        const double t = dist(zu, zv, d);
+        if (t == 0.0) return;                 /* the force vanishes with t */
+        double scal, c, dc;                   /* c = scal / t; dc = dc/d(t^2) */
+        if (model == ORC_FR) {
+            scal = t * t;
+            c = t;
+            dc = 1.0 / (2.0 * t);
+        } else if (model == ORC_LINLOG) {
+            scal = log(1.0 + t);
+            c = scal / t;
+            dc = (t / (1.0 + t) - scal) / (2.0 * t * t * t);
+        } else {                              /* ForceAtlas */
+            scal = t;
+            c = 1.0;
+            dc = 0.0;
+        }
+        for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zv[j]) / t;
+        if (gabs) {
+            double df[d];
+            for (int32_t j = 0; j < d; ++j) df[j] = zu[j] - zv[j];
+            add_scale(gabs, df, d, c, dc, t * t);
+        }
     } else {
         /* Eq. 8: 2t / (1 + t^2), times the unit vector (z_u - z_v)/t (Sec. III-B) */
         const double t = dist(zu, zv, d);
@@ -261,6 +306,19 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
         const double c = sigma(x);
         for (int32_t j = 0; j < d; ++j) g[j] += c * zw[j];
         if (gabs) add_scale(gabs, zw, d, c, sigma(x) * (1.0 - sigma(x)), dot_abs(zu, zw, d));
+    } else if (model != ORC_TDIST) {
+        /* Table "diffmodels", all three models: minus the force 1/t times
+           the unit vector, with t^2 floored at 1e-8 */
+        double t = dist(zu, zw, d);
+        double t2 = t * t;
+        if (t2 < ORC_T2_FLOOR) { t2 = ORC_T2_FLOOR; t = sqrt(t2); }
+        const double scal = -1.0 / t;
+        for (int32_t j = 0; j < d; ++j) g[j] += scal * (zu[j] - zw[j]) / t;
+        if (gabs) {
+            double df[d];
+            for (int32_t j = 0; j < d; ++j) df[j] = zu[j] - zw[j];
+            add_scale(gabs, df, d, 1.0 / t2, 1.0 / (t2 * t2), t2);
+        }
     } else {
         /* Eq. 9: -2 / (t (1 + t^2)), times the unit vector (z_u - z_w)/t,
            with t^2 floored at 1e-8 */
@@ -404,7 +462,7 @@ int orc_train_walk(int model, int64_t n, int32_t d,
             for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
                 for (int32_t j = 0; j < d; ++j) {
                     double z = Z[u * d + j] - eta * grad[(u - u0) * d + j];
-                    if (model == ORC_SIGMOID) {              /* bounded coordinates */
+                    if (model != ORC_TDIST) {                /* bounded coordinates */
                         if (z > ORC_SIGMOID_BOUND) z = ORC_SIGMOID_BOUND;
                         if (z < -ORC_SIGMOID_BOUND) z = -ORC_SIGMOID_BOUND;
                     }
