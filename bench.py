@@ -40,12 +40,15 @@ import numpy as np  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2009_10035_gb300/csrc/f2v_bulk.cuh",
+                  "paper_2009_10035_gb300/csrc/f2v_bulk_fp32.cu",
                   "paper_2009_10035_gb300/csrc/f2v_force.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_device.cuh",
                   "paper_2009_10035_gb300/csrc/f2v_force_fp32.cu",
                   "paper_2009_10035_gb300/csrc/f2v_expand.cu",
                   "paper_2009_10035_gb300/csrc/f2v_tmap.cu"]
 FALLBACK_HBM_GBS = 6800.0
+# force models of include/f2v.h (f2v_model)
+MODEL_IDS = {"tdist": 0, "sigmoid": 1, "fr": 2, "linlog": 3, "forceatlas": 4}
 
 
 def parse():
@@ -55,7 +58,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--scale", type=int, default=20)
-    ap.add_argument("--model", choices=["tdist", "sigmoid"], default="tdist")
+    ap.add_argument("--model", choices=list(MODEL_IDS), default="tdist",
+                    help="force model (fr, linlog, forceatlas: single-graph workload only)")
     ap.add_argument("--walk", type=int, default=0,
                     help="rForce2Vec walk length (0: 1-hop neighbourhoods)")
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
@@ -223,7 +227,7 @@ def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None, wal
 def run_reference(args, g, world, rank):
     if rank != 0:
         return
-    model = 0 if args.model == "tdist" else 1
+    model = MODEL_IDS[args.model]
     import oracle
     threads = oracle.set_threads(0)
     d, s, b, seed = 128, 5, 4096, 1
@@ -278,7 +282,7 @@ def run_ours(args, g, world, rank, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     d, s, b, seed, lr = 128, 5, 4096, 1, 0.02
-    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    model = MODEL_IDS[args.model]
     total_epochs = max(20, args.warmup + args.steps)
 
     def make(m):
@@ -359,7 +363,7 @@ def run_ours(args, g, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms2 = e0.elapsed_time(e1)
-        name = "sigmoid" if other == f2v.SIGMOID else "tdist"
+        name = {v: k for k, v in MODEL_IDS.items()}[other]
         extra[name] = {"value": P * args.steps / (ms2 / 1e3), "ms_per_step": ms2 / args.steps}
         c2.close()
 
@@ -458,7 +462,7 @@ def run_batched(args, world, rank, local):
     from paper_2009_10035_gb300 import f2v, graphs
 
     torch.cuda.set_device(local)
-    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    model = MODEL_IDS[args.model]
     gb = graphs.sbm_batch(args.graphs, seed=1 + rank)
     s, b, lr = 5, 128, 0.02
     bt = f2v.Batch.from_graphs(gb, model=model, s=s, lr=lr, minibatch=b)
@@ -579,7 +583,7 @@ def run_precision(args, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    model = MODEL_IDS[args.model]
     d, s, b, lr, E = 128, 10, 16384, 0.02, 10
     t0 = time.perf_counter()
     g = graphs.rmat(23, 16, seed=1)
@@ -692,7 +696,7 @@ def run_served(args, world, rank, local):
     from paper_2009_10035_gb300 import f2v
 
     torch.cuda.set_device(local)
-    model = f2v.TDIST if args.model == "tdist" else f2v.SIGMOID
+    model = MODEL_IDS[args.model]
     t_pool = time.perf_counter()
     pool = serve_pool()
     pinned = {sc: (torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col_idx).pin_memory())

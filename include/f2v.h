@@ -61,7 +61,23 @@ typedef enum {
     F2V_ESTATE = 5     /* context already failed, or call not valid now */
 } f2v_status;
 
-typedef enum { F2V_TDIST = 0, F2V_SIGMOID = 1 } f2v_model;
+/* Force model.  F2V_TDIST: t-distribution, Eq. 8/9 times the unit vector
+   (Sec. III-B).  F2V_SIGMOID: Eq. 5/6.  F2V_FR, F2V_LINLOG, F2V_FORCEATLAS:
+   Fruchterman-Reingold, LinLog, ForceAtlas (Table "diffmodels"): the
+   table's force on u along the unit vector (z_u - z_x)/t, t = |z_u - z_x|,
+   is -t^2, -log(1 + t), -t for a neighbour and 1/t for a sample; Eq. 10
+   steps against the gradient, so a pair adds minus that force times the
+   unit vector: t (z_u - z_v), log(1 + t)/t (z_u - z_v), (z_u - z_v), and
+   -(z_u - z_w)/t^2 for a sample (t^2 floored at 1e-8, as in the t model).
+   Every model but F2V_TDIST bounds each coordinate of an updated row to
+   [-4, 4] (their forces do not vanish with distance). */
+typedef enum {
+    F2V_TDIST = 0,
+    F2V_SIGMOID = 1,
+    F2V_FR = 2,
+    F2V_LINLOG = 3,
+    F2V_FORCEATLAS = 4
+} f2v_model;
 
 /* Storage of Z.  F2V_FP32: Z in FP32.  F2V_BF16: gathered rows stored in
    BF16 with an FP32 master copy; forces are accumulated and the update
@@ -173,7 +189,7 @@ f2v_status f2v_set_stream(f2v_ctx *ctx, void *stream);
 /*
  * Link-prediction AUC of the current Z on held-out pairs: pos_pairs[2*npos]
  * and neg_pairs[2*nneg] are host int32 (u, v) pairs.  Score of a pair:
- * z_u . z_v (sigmoid model) or -||z_u - z_v||^2 (t model), computed in FP64
+ * z_u . z_v (sigmoid model) or -||z_u - z_v||^2 (the other models), in FP64
  * from the stored rows on the device; AUC = (#{pos > neg} + #{pos == neg}/2)
  * / (npos * nneg), with the counts reduced exactly in integers.  Synchronous.
  */

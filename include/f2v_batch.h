@@ -64,7 +64,8 @@ typedef struct {
  * validates and copies the concatenated host CSRs (layout above), allocates
  * every graph's Z (two buffers of n[g] x d[g] in the storage precision, plus
  * an FP32 master in the BF16 form) and draws each Z0 from seed[g].  The
- * shared parameters follow f2v_create: model, 0 <= s <= 65534, lr > 0 finite
+ * shared parameters follow f2v_create: model (F2V_TDIST or F2V_SIGMOID; the
+ * other force models are single-graph only), 0 <= s <= 65534, lr > 0 finite
  * (constant schedule until f2v_batch_set_schedule), minibatch >= 1, and the
  * storage precision.  `stream` is a cudaStream_t or NULL (the batch then
  * creates its own non-blocking stream).  Epoch counters start at 0.

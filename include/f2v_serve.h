@@ -41,7 +41,7 @@ typedef struct {
     const int32_t *row_ptr;
     const int32_t *col_idx;
     int32_t n, d;
-    f2v_model model;
+    f2v_model model;        /* F2V_TDIST or F2V_SIGMOID */
     int32_t s;
     float lr;               /* eta_0; decayed linearly over `epochs` */
     int32_t minibatch;

@@ -664,7 +664,7 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
     if (s < 0 || s > 65534) return fail(nullptr, F2V_EINVAL, "s = %d, must be in [0, 65534]", s);
     if (minibatch < 1) return fail(nullptr, F2V_EINVAL, "minibatch = %d, must be >= 1", minibatch);
     if (!(lr > 0.f) || !std::isfinite(lr)) return fail(nullptr, F2V_EINVAL, "lr must be finite and > 0");
-    if (model != F2V_TDIST && model != F2V_SIGMOID) return fail(nullptr, F2V_EINVAL, "unknown model %d", (int)model);
+    if (model < F2V_TDIST || model > F2V_FORCEATLAS) return fail(nullptr, F2V_EINVAL, "unknown model %d", (int)model);
     if (precision != F2V_FP32 && precision != F2V_BF16) return fail(nullptr, F2V_EINVAL, "unknown precision %d", (int)precision);
     f2v_status st = validate_graph(row_ptr, col_idx, n, flags);
     if (st != F2V_OK) return st;

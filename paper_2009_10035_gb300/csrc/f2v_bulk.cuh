@@ -267,7 +267,10 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
     int *vert = reinterpret_cast<int *>(wsm + Lay::VERT_OFF);
     int *vends = reinterpret_cast<int *>(wsm + Lay::VEND_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + Lay::BAR_OFF);
-    constexpr bool tdist = (MODEL == 0);            // the force model, fixed per instantiation
+    // the force model class, fixed per instantiation: every model but the
+    // sigmoid reduces a squared distance and accumulates c (z_u - x)
+    constexpr bool tdist = (MODEL != 1);
+    const int model = model_of<MODEL>(a.f.model);
     const int flag_value = (int)a.f.epoch + 1;
 
     // zero the staging buffers once, so rows that are never copied are finite
@@ -452,19 +455,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
         {
             const float sdot = p[0];
             float coef = 0.f;
-            if (tkind != KIND_NONE) {
-                if (tdist) {
-                    if (tkind == KIND_ATTR) {
-                        coef = 2.f / (1.f + sdot);                 // Eq. 8 / t
-                    } else {
-                        const float q2 = fmaxf(sdot, kT2Floor);
-                        coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
-                    }
-                } else {
-                    coef = (tkind == KIND_ATTR) ? -1.f / (1.f + expf(sdot))   // Eq. 5
-                                                : 1.f / (1.f + expf(-sdot));  // Eq. 6
-                }
-            }
+            if (tkind != KIND_NONE) coef = pair_coef(model, tkind, sdot);   // Eq. 5/6, 8/9, Table "diffmodels"
             coefs[lane] = coef;              // 0 for pairs without a force
         }
         __syncwarp();
@@ -630,40 +621,45 @@ cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const
     return cudaGetLastError();
 }
 
+template <int D, typename Ts>
+cudaError_t launch_bulk_m(int model, const EpochArgs<Ts> &a, const CUtensorMap &zmap,
+                          const CUtensorMap &mmap, int blocks, int warps, int smem,
+                          cudaStream_t st)
+{
+    if (model == 0) return launch_bulk_d<D, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st);
+    if (model == 1) return launch_bulk_d<D, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
+    return launch_bulk_d<D, Ts, kModelOther>(a, zmap, mmap, blocks, warps, smem, st);
+}
+
 template <typename Ts>
 cudaError_t launch_bulk_t(int d, int model, const EpochArgs<Ts> &a, const CUtensorMap &zmap,
                           const CUtensorMap &mmap, int blocks, int warps, int smem,
                           cudaStream_t st)
 {
-    const bool t = (model == 0);
     switch (d) {
-        case 64:
-            return t ? launch_bulk_d<64, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
-                     : launch_bulk_d<64, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
-        case 128:
-            return t ? launch_bulk_d<128, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
-                     : launch_bulk_d<128, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
-        case 256:
-            return t ? launch_bulk_d<256, Ts, 0>(a, zmap, mmap, blocks, warps, smem, st)
-                     : launch_bulk_d<256, Ts, 1>(a, zmap, mmap, blocks, warps, smem, st);
+        case 64: return launch_bulk_m<64, Ts>(model, a, zmap, mmap, blocks, warps, smem, st);
+        case 128: return launch_bulk_m<128, Ts>(model, a, zmap, mmap, blocks, warps, smem, st);
+        case 256: return launch_bulk_m<256, Ts>(model, a, zmap, mmap, blocks, warps, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Blocks per SM: the smaller of the two models' (they differ only in code).
+// Blocks per SM: the smallest of the model classes' (they differ only in code).
+template <int D, typename Ts>
+int bulk_resident_m(int warps, int smem)
+{
+    return std::min(std::min(bulk_resident_d<D, Ts, 0>(warps, smem),
+                             bulk_resident_d<D, Ts, 1>(warps, smem)),
+                    bulk_resident_d<D, Ts, kModelOther>(warps, smem));
+}
+
 template <typename Ts>
 int bulk_resident_t(int d, int warps, int smem)
 {
     switch (d) {
-        case 64:
-            return std::min(bulk_resident_d<64, Ts, 0>(warps, smem),
-                            bulk_resident_d<64, Ts, 1>(warps, smem));
-        case 128:
-            return std::min(bulk_resident_d<128, Ts, 0>(warps, smem),
-                            bulk_resident_d<128, Ts, 1>(warps, smem));
-        case 256:
-            return std::min(bulk_resident_d<256, Ts, 0>(warps, smem),
-                            bulk_resident_d<256, Ts, 1>(warps, smem));
+        case 64: return bulk_resident_m<64, Ts>(warps, smem);
+        case 128: return bulk_resident_m<128, Ts>(warps, smem);
+        case 256: return bulk_resident_m<256, Ts>(warps, smem);
         default: return 0;
     }
 }

@@ -14,10 +14,10 @@
 //      from the epoch's expanded partner list;
 //   2. gather -- the group fetches the partner rows, U at a time, each lane
 //      a VEC-wide vector of NV slices (128-bit loads for FP32 rows of d >= 4);
-//   3. force -- the dot product (sigmoid) or squared distance (t model) is
-//      reduced with xor shuffles inside the group, turned into the scalar of
-//      Eq. 5/6 or Eq. 8/9, and the scaled row is accumulated in FP32
-//      registers (the SpMM half);
+//   3. force -- the dot product (sigmoid) or squared distance (the other
+//      models) is reduced with xor shuffles inside the group, turned into the
+//      scalar of Eq. 5/6, Eq. 8/9 or Table "diffmodels" (pair_coef), and the
+//      scaled row is accumulated in FP32 registers (the SpMM half);
 //   4. update -- when a vertex's pairs end, z_u - eta * g is written to the
 //      next buffer, directly if the item held all its pairs, else through the
 //      ordered combine tree described in f2v_internal.h.
@@ -39,6 +39,44 @@ constexpr int KIND_ATTR = 1;   // neighbour: attractive force
 constexpr int KIND_REP = 2;    // negative sample: repulsive force
 constexpr float kT2Floor = 1e-8f;
 constexpr float kSigmoidBound = 4.f;
+
+// Force models (f2v_model): 0 t-distribution, 1 sigmoid, 2 Fruchterman-
+// Reingold, 3 LinLog, 4 ForceAtlas.  Kernels are instantiated per model
+// class: MODEL = 0 (t), 1 (sigmoid), 2 (FR, LinLog or ForceAtlas, chosen by
+// ForceArgs::model at run time; they share every loop and differ only in the
+// attraction scalar), or -1 (everything read at run time).
+constexpr int kModelOther = 2;
+
+// The model a kernel instantiation computes.
+template <int MODEL>
+__device__ __forceinline__ int model_of(int rt_model)
+{
+    return (MODEL == 0 || MODEL == 1) ? MODEL : rt_model;
+}
+
+// Force scalar c of one pair from its reduced scalar r: the dot product
+// z_u . z_x for the sigmoid model (term c z_x), the squared distance
+// q = |z_u - z_x|^2 for the others (term c (z_u - z_x)):
+//   t model, Eq. 8/9 times the unit vector:      2/(1+q),  -2/(q(1+q))
+//   FR, LinLog, ForceAtlas, minus the force of Table "diffmodels" times the
+//   unit vector:  t = sqrt(q), log(1+t)/t, 1;    -1/q
+// (q floored at 1e-8 in the repulsive terms).
+__device__ __forceinline__ float pair_coef(int model, int kind, float r)
+{
+    if (model == 1)
+        return (kind == KIND_ATTR) ? -1.f / (1.f + expf(r))     // Eq. 5
+                                   : 1.f / (1.f + expf(-r));    // Eq. 6
+    if (kind == KIND_ATTR) {
+        if (model == 0) return 2.f / (1.f + r);                  // Eq. 8 / t
+        const float t = sqrtf(r);
+        if (model == 2) return t;                                // FR: t^2 / t
+        if (model == 3) return t > 0.f ? log1pf(t) / t : 1.f;    // LinLog
+        return 1.f;                                              // ForceAtlas: t / t
+    }
+    const float q2 = fmaxf(r, kT2Floor);
+    return (model == 0) ? -2.f / (q2 * (1.f + q2))               // Eq. 9 / t
+                        : -1.f / q2;                             // (1/t) / t
+}
 
 template <int L, int VEC, int NV>
 struct ShapeTraits {
@@ -140,9 +178,10 @@ __device__ __forceinline__ void write_row(const ForceArgs<Ts> &a, const FinishCt
     float z[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) z[e] = fmaf(-a.eta, g[e], zu[e]);
-    // sigmoid model: coordinates bounded to [-4, 4] (without a bound the
-    // summed gradients of a high-degree vertex make Alg. 1 diverge)
-    if (MODEL == 1 || (MODEL < 0 && a.model == 1)) {
+    // every model but t: coordinates bounded to [-4, 4] (their forces do
+    // not vanish with distance; without a bound the summed gradients of a
+    // high-degree vertex make Alg. 1 diverge)
+    if (MODEL > 0 || (MODEL < 0 && a.model != 0)) {
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = fminf(fmaxf(z[e], -kSigmoidBound), kSigmoidBound);
     }
@@ -281,7 +320,8 @@ __device__ __forceinline__ void force_item_lane(const ForceArgs<Ts> &a, const Fi
 {
     constexpr int E = VEC * NV;
     constexpr int T = 8;
-    const bool tdist = (MODEL >= 0) ? (MODEL == 0) : (a.model == 0);
+    const int model = model_of<MODEL>(a.model);
+    const bool dist = (model != 1);       // squared distance, else dot product
     const int q_begin = item * a.C;
     const int q_end = min(q_begin + a.C, a.Pk);
     int u = __ldg(&a.item_u0[item]);
@@ -325,26 +365,19 @@ __device__ __forceinline__ void force_item_lane(const ForceArgs<Ts> &a, const Fi
         for (int i = 0; i < T; ++i) {
             if (kd[i] == KIND_NONE) continue;
             float part = 0.f;
-            if (tdist) {
+            if (dist) {
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const float df = zu[e] - zv[i][e];
                     part = fmaf(df, df, part);
                 }
-                float coef;
-                if (kd[i] == KIND_ATTR) {
-                    coef = 2.f / (1.f + part);                 // Eq. 8 / t
-                } else {
-                    const float q2 = fmaxf(part, kT2Floor);
-                    coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
-                }
+                const float coef = pair_coef(model, kd[i], part);
 #pragma unroll
                 for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
             } else {
 #pragma unroll
                 for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
-                const float coef = (kd[i] == KIND_ATTR) ? -1.f / (1.f + expf(part))    // Eq. 5
-                                                        : 1.f / (1.f + expf(-part));   // Eq. 6
+                const float coef = pair_coef(1, kd[i], part);
 #pragma unroll
                 for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
             }
@@ -378,8 +411,9 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
         force_item_lane<VEC, NV, EXACT, COHERENT, MODEL>(a, fc, item, gmask);
         return;
     }
-    // the force model: fixed per instantiation when MODEL >= 0
-    const bool tdist = (MODEL >= 0) ? (MODEL == 0) : (a.model == 0);
+    // the force model: fixed per instantiation when MODEL is 0 or 1
+    const int model = model_of<MODEL>(a.model);
+    const bool dist = (model != 1);       // squared distance, else dot product
     const int q_begin = item * a.C;
     const int q_end = min(q_begin + a.C, a.Pk);
     int u = __ldg(&a.item_u0[item]);       // vertex holding pair q_begin
@@ -483,7 +517,7 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
             for (int i = 0; i < U; ++i) {
                 if (kr[i] == KIND_NONE) continue;
                 float part = 0.f;
-                if (tdist) {
+                if (dist) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const float df = zu[e] - zv[i][e];
@@ -496,20 +530,11 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
 #pragma unroll
                 for (int m = L / 2; m >= 1; m >>= 1)
                     part += __shfl_xor_sync(gmask, part, m, L);
-                if (tdist) {
-                    float coef;
-                    if (kr[i] == KIND_ATTR) {
-                        coef = 2.f / (1.f + part);                 // Eq. 8 / t
-                    } else {
-                        const float q2 = fmaxf(part, kT2Floor);
-                        coef = -2.f / (q2 * (1.f + q2));           // Eq. 9 / t
-                    }
+                const float coef = pair_coef(model, kr[i], part);
+                if (dist) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
                 } else {
-                    const float coef = (kr[i] == KIND_ATTR)
-                                           ? -1.f / (1.f + expf(part))    // Eq. 5
-                                           : 1.f / (1.f + expf(-part));   // Eq. 6
 #pragma unroll
                     for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zv[i][e], g[e]);
                 }
@@ -547,8 +572,10 @@ cudaError_t launch_shape(const ForceArgs<Ts> &a, int blocks_cap, cudaStream_t st
     if (blocks < 1) blocks = 1;
     if (a.model == 0)
         force_kernel<L, VEC, NV, EXACT, 0, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-    else
+    else if (a.model == 1)
         force_kernel<L, VEC, NV, EXACT, 1, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else
+        force_kernel<L, VEC, NV, EXACT, kModelOther, Ts><<<(unsigned)blocks, kBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 

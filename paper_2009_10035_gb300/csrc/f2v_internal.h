@@ -146,6 +146,7 @@ int items_pairs(const Shape &sh);
 bool bulk_config(int d, bool bf16, int *warps_per_block, int *smem_bytes);
 // Blocks of that kernel resident per SM (0 if it cannot run).
 int bulk_resident(int d, bool bf16, int warps, int smem_bytes);
+int bulk_resident_bf16(int d, int warps, int smem_bytes);
 // `zmap` covers both Z buffers (2n rows of the storage type); `mmap` the FP32
 // own rows (the master in the BF16 form, zmap again in the FP32 form).
 // `model` selects the instantiation (0 t-distribution, 1 sigmoid).

@@ -141,7 +141,7 @@ extern "C" f2v_status f2v_minibatch_noalloc(const int32_t *row_ptr, const int32_
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: a pointer is NULL");
     if (n < 1 || d < 1 || d > 1024 || s < 0 || s > 65534 || epoch < 0)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: n, d, s or epoch out of range");
-    if (model != F2V_TDIST && model != F2V_SIGMOID)
+    if (model < F2V_TDIST || model > F2V_FORCEATLAS)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: unknown model");
     if (!(eta > 0.f) || eta != eta || eta > 3.0e38f)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: eta must be finite and > 0");

@@ -15,6 +15,9 @@ import numpy as np
 
 TDIST = 0
 SIGMOID = 1
+FR = 2              # Fruchterman-Reingold
+LINLOG = 3
+FORCEATLAS = 4
 FP32 = 0
 BF16 = 1
 LR_CONSTANT = 0

@@ -97,7 +97,7 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
                 eta = oracle.learning_rate(lr, 0 if schedule is None else schedule,
                                            total_epochs, e)
                 want = before[u0:u1] - eta * G
-                if model == f2v.SIGMOID:
+                if model != f2v.TDIST:
                     want = np.clip(want, -4.0, 4.0)
                 scale = np.maximum(np.abs(before[u0:u1]) + eta * A, FLOOR)
                 err = np.abs(after[u0:u1] - want) / scale
@@ -487,3 +487,62 @@ def test_rmat_scale20_d128_walk_steps(model, rmat20):
     worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps, walk=5,
                         schedule=f2v.LR_LINEAR, total_epochs=20)
     print(f"rmat20 walks model={model}: worst scaled error {worst:.3e}")
+
+
+# ---------------------------------------------------------------- Table "diffmodels"
+
+OTHER_MODELS = [pytest.param(f2v.FR, id="fr"), pytest.param(f2v.LINLOG, id="linlog"),
+                pytest.param(f2v.FORCEATLAS, id="forceatlas")]
+
+
+@pytest.mark.parametrize("model", OTHER_MODELS)
+@pytest.mark.parametrize("d", [4, 8, 32, 128])
+def test_other_models_steps(model, d):
+    """FR, LinLog and ForceAtlas, one launch at a time: register kernel
+    (d = 4, 8, 32) and staged kernel (d = 128)."""
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, d, model, 4, 256, lr=0.01, seed=4, epochs=2,
+                steps={(0, 0), (0, 3), (1, 2), (1, 5)})
+
+
+@pytest.mark.parametrize("model", OTHER_MODELS)
+def test_other_models_register_kernel_and_bf16_at_d128(model):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, 128, model, 4, 256, lr=0.01, seed=4, epochs=1, steps={(0, 0), (0, 4)},
+                flags=f2v.FLAG_NO_STAGING)
+    check_steps(g, 128, model, 4, 256, lr=0.01, seed=4, epochs=1, steps={(0, 1), (0, 5)},
+                precision=f2v.BF16)
+
+
+@pytest.mark.parametrize("model", OTHER_MODELS)
+def test_other_models_one_epoch(model):
+    g = graphs.config1_graph()
+    check_parity(g, 32, model, 5, 256, lr=0.01)
+
+
+@pytest.mark.parametrize("model", OTHER_MODELS)
+def test_other_models_with_walks(model):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, 128, model, 4, 256, lr=0.01, seed=4, epochs=1, walk=5, steps={(0, 2)})
+
+
+def test_unknown_model_and_batched_other_models_are_rejected():
+    g = graphs.erdos_renyi(100, p=0.05, seed=1)
+    with pytest.raises(f2v.F2VError):
+        f2v.Context(g.row_ptr, g.col_idx, g.n, 8, model=5)
+    with pytest.raises(f2v.F2VError):
+        f2v.Batch(np.array([g.n], np.int32), np.array([8], np.int32), np.array([1], np.uint64),
+                  g.row_ptr, g.col_idx, model=f2v.FR)
+
+
+@pytest.mark.parametrize("model", OTHER_MODELS)
+def test_rmat_scale20_d128_other_models(model, rmat20):
+    """The benchmark graph and launch configuration, sampled launches."""
+    g = rmat20
+    b = 4096
+    M = -(-g.n // b)
+    hub_mb = int(np.argmax(g.degrees())) // b
+    steps = {(0, 0), (0, hub_mb), (0, M - 1)}
+    worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps,
+                        schedule=f2v.LR_LINEAR, total_epochs=20)
+    print(f"rmat20 model={model}: worst scaled error {worst:.3e}")
