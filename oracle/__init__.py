@@ -15,6 +15,7 @@ Every function cites the passage it follows:
                   generator both sides implement from its published definition
   init_embedding  Sec. III-C "Initialization": random Z, uniform [-0.5, 0.5)
   samples         negative samples, s per vertex (Sec. III-C complexity text)
+  samples_shared  the literal Alg. 1 line 6: one set S_b per minibatch
   grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t),
                   Table "diffmodels" (FR, LinLog, ForceAtlas)
   walk            Algorithm 3 (GenWalk), the rForce2Vec neighbourhood
@@ -89,15 +90,16 @@ def _load():
         lib.orc_grad_minibatch_abs.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp, i64,
                                                i64, i32, u64, i32, vp, vp, vp, vp]
         lib.orc_grad_minibatch_abs.restype = None
-        lib.orc_grad_minibatch_walk_abs.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp,
-                                                    i64, i64, i32, i32, u64, i32, vp, vp, vp,
-                                                    vp]
-        lib.orc_grad_minibatch_walk_abs.restype = None
+        lib.orc_grad_minibatch_ex.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp, i64, i64,
+                                              i32, i32, i64, u64, i32, vp, vp, vp, vp]
+        lib.orc_grad_minibatch_ex.restype = None
+        lib.orc_sample_shared.argtypes = [u64, u32, u32, u32, u32]
+        lib.orc_sample_shared.restype = u32
         lib.orc_walk.argtypes = [u64, vp, vp, i64, i32, i32, vp]
         lib.orc_walk.restype = None
-        lib.orc_train_walk.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i32, i64, u64,
-                                       f64, i32, i32, i32, i32, i64, vp, vp]
-        lib.orc_train_walk.restype = ctypes.c_int
+        lib.orc_train_ex.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i32, i32, i64,
+                                     u64, f64, i32, i32, i32, i32, i64, vp, vp]
+        lib.orc_train_ex.restype = ctypes.c_int
         lib.orc_learning_rate.argtypes = [f64, i32, i32, i32]
         lib.orc_learning_rate.restype = f64
         lib.orc_train.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i64, u64,
@@ -184,21 +186,34 @@ def walk(row_ptr, col_idx, u: int, epoch: int, k: int, seed: int) -> np.ndarray:
     return out[:k]
 
 
+def samples_shared(n: int, s: int, b: int, epoch: int, seed: int) -> np.ndarray:
+    """The literal Algorithm 1 line 6: row u lists the set S_b of u's
+    minibatch (k = u // b), an n x s int32 array."""
+    lib = _load()
+    out = np.zeros((n, s), dtype=np.int32)
+    for u in range(0, n, b):
+        row = [lib.orc_sample_shared(seed, u // b, epoch, j, n) for j in range(s)]
+        out[u:min(n, u + b)] = row
+    return out
+
+
 def grad_minibatch(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
-                   injected=None, walk=0) -> np.ndarray:
+                   injected=None, walk=0, shared_b=0) -> np.ndarray:
     """Algorithm 2 for the vertices [u_begin, u_end); returns (u_end-u_begin) x d.
-    walk > 0: N(u) from Algorithm 3 (rForce2Vec)."""
+    walk > 0: N(u) from Algorithm 3 (rForce2Vec).  shared_b > 0: every
+    vertex of minibatch k = u // shared_b uses that minibatch's sample set."""
     return grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
-                              injected=injected, walk=walk)[0]
+                              injected=injected, walk=walk, shared_b=shared_b)[0]
 
 
 def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoch,
-                       injected=None, gather=None, walk=0):
+                       injected=None, gather=None, walk=0, shared_b=0):
     """Algorithm 2 for [u_begin, u_end): returns (grad, grad_abs), where
     grad_abs sums the absolute values of the per-pair terms element by
     element (the scale of the rounding error of an FP32 evaluation).  With
     `gather`, partner rows come from that matrix and only z_u from Z.
-    walk > 0: N(u) from Algorithm 3 (rForce2Vec)."""
+    walk > 0: N(u) from Algorithm 3 (rForce2Vec).  shared_b > 0: shared
+    sample sets of minibatches of that size."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.ascontiguousarray(Z, dtype=np.float64)
@@ -208,10 +223,9 @@ def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoc
     sp, si = _injected(injected)
     g = np.zeros((u_end - u_begin, d), dtype=np.float64)
     ga = np.zeros((u_end - u_begin, d), dtype=np.float64)
-    lib.orc_grad_minibatch_walk_abs(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
-                                    None if Zp is None else _ptr(Zp), u_begin, u_end, s,
-                                    int(walk), seed, epoch, _ptr(sp), _ptr(si), _ptr(g),
-                                    _ptr(ga))
+    lib.orc_grad_minibatch_ex(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
+                              None if Zp is None else _ptr(Zp), u_begin, u_end, s, int(walk),
+                              int(shared_b), seed, epoch, _ptr(sp), _ptr(si), _ptr(g), _ptr(ga))
     return g, ga
 
 
@@ -221,17 +235,18 @@ def learning_rate(lr0: float, schedule: int, total_epochs: int, epoch: int) -> f
 
 def train(model, row_ptr, col_idx, Z, s, b, seed, lr, epochs, start_epoch=0,
           schedule=0, total_epochs=0, max_minibatches=-1, injected=None,
-          walk=0) -> np.ndarray:
+          walk=0, shared=False) -> np.ndarray:
     """Algorithm 1 from embedding Z (copied); returns the new FP64 embedding.
-    walk > 0: rForce2Vec, N(u) from Algorithm 3 with walks of that length."""
+    walk > 0: rForce2Vec, N(u) from Algorithm 3 with walks of that length.
+    shared: one sample set S_b per minibatch (the literal line 6)."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.array(Z, dtype=np.float64, order="C", copy=True)
     n, d = Z.shape
     sp, si = _injected(injected)
-    rc = lib.orc_train_walk(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), s, int(walk),
-                            b, seed, lr, schedule, total_epochs, start_epoch, epochs,
-                            max_minibatches, _ptr(sp), _ptr(si))
+    rc = lib.orc_train_ex(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), s, int(walk),
+                          int(bool(shared)), b, seed, lr, schedule, total_epochs, start_epoch,
+                          epochs, max_minibatches, _ptr(sp), _ptr(si))
     if rc != 0:
         raise MemoryError("oracle train: out of memory")
     return Z

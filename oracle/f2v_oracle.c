@@ -18,6 +18,9 @@
  *   orc_sample          uniform negative sample for vertex u (Sec. III-C,
  *                       negative sampling; one set of s samples per vertex as
  *                       in the complexity paragraph of Sec. III-C).
+ *   orc_sample_shared   the literal form of Alg. 1 line 6: one set S_b of s
+ *                       samples per minibatch, used by every vertex of it
+ *                       (Sec. III-C, the paragraph after Alg. 1).
  *   attractive_grad,    per-pair gradients: sigmoid model Eq. 5 / Eq. 6,
  *   repulsive_grad      t-distribution model Eq. 8 / Eq. 9, each times the
  *                       unit vector of Sec. III-B for the t model; the
@@ -70,6 +73,9 @@
  *     Their forces grow (FR, LinLog, ForceAtlas attraction) or stay finite
  *     with distance, so like the sigmoid model they take the coordinate
  *     bound below.
+ *   - Shared samples (the literal Alg. 1 line 6, an option): sample j of
+ *     minibatch k in epoch e is Philox(key, ctr=(k, e, j, 2)).x0 mod n for
+ *     every vertex of the minibatch; a sample equal to u adds no force.
  *   - Sigmoid (and FR, LinLog, ForceAtlas) models: after each update every
  *     coordinate of z_u is clamped to
  *     [-4, 4].  The paper is silent on divergence; without a bound, Alg. 1 at
@@ -167,6 +173,11 @@ void orc_init_embedding(int64_t n, int32_t d, uint64_t seed, double *Z)
 uint32_t orc_sample(uint64_t seed, uint32_t u, uint32_t epoch, uint32_t k, uint32_t n)
 {
     return philox_x0(seed, u, epoch, k, 0u) % n;
+}
+
+uint32_t orc_sample_shared(uint64_t seed, uint32_t k, uint32_t epoch, uint32_t j, uint32_t n)
+{
+    return philox_x0(seed, k, epoch, j, 2u) % n;
 }
 
 void orc_samples(uint64_t seed, int64_t n, int32_t s, int32_t epoch, int32_t *out)
@@ -352,13 +363,14 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
  * precision copy of each vertex's own row.
  */
 /* walk > 0: N(u) is the walk of Algorithm 3 (rForce2Vec) instead of the
-   neighbours of u. */
-void orc_grad_minibatch_walk_abs(int model, int64_t n, int32_t d,
-                                 const int32_t *row_ptr, const int32_t *col_idx,
-                                 const double *Z, const double *Zp, int64_t u_begin,
-                                 int64_t u_end, int32_t s, int32_t walk, uint64_t seed,
-                                 int32_t epoch, const int64_t *samp_ptr,
-                                 const int32_t *samp_idx, double *grad, double *grad_abs)
+   neighbours of u.  shared_b > 0: the samples of u are the set S_b of its
+   minibatch k = u / shared_b (orc_sample_shared) instead of its own. */
+void orc_grad_minibatch_ex(int model, int64_t n, int32_t d,
+                           const int32_t *row_ptr, const int32_t *col_idx,
+                           const double *Z, const double *Zp, int64_t u_begin,
+                           int64_t u_end, int32_t s, int32_t walk, int64_t shared_b,
+                           uint64_t seed, int32_t epoch, const int64_t *samp_ptr,
+                           const int32_t *samp_idx, double *grad, double *grad_abs)
 {
     if (Zp == NULL) Zp = Z;
     #pragma omp parallel for schedule(dynamic, 16)
@@ -384,8 +396,11 @@ void orc_grad_minibatch_walk_abs(int model, int64_t n, int32_t d,
         }
         if (samp_ptr == NULL) {
             for (int32_t k = 0; k < s; ++k) {
-                const int64_t w = orc_sample(seed, (uint32_t)u, (uint32_t)epoch,
-                                             (uint32_t)k, (uint32_t)n);
+                const int64_t w =
+                    shared_b > 0 ? orc_sample_shared(seed, (uint32_t)(u / shared_b),
+                                                     (uint32_t)epoch, (uint32_t)k, (uint32_t)n)
+                                 : orc_sample(seed, (uint32_t)u, (uint32_t)epoch, (uint32_t)k,
+                                              (uint32_t)n);
                 if (w == u) continue;
                 repulsive_grad(model, zu, Zp + w * d, d, gr, gabs);
             }
@@ -408,8 +423,8 @@ void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
                             const int64_t *samp_ptr, const int32_t *samp_idx,
                             double *grad, double *grad_abs)
 {
-    orc_grad_minibatch_walk_abs(model, n, d, row_ptr, col_idx, Z, Zp, u_begin, u_end, s, 0,
-                                seed, epoch, samp_ptr, samp_idx, grad, grad_abs);
+    orc_grad_minibatch_ex(model, n, d, row_ptr, col_idx, Z, Zp, u_begin, u_end, s, 0, 0, seed,
+                          epoch, samp_ptr, samp_idx, grad, grad_abs);
 }
 
 void orc_grad_minibatch(int model, int64_t n, int32_t d,
@@ -438,15 +453,16 @@ double orc_learning_rate(double lr0, int32_t schedule, int32_t total_epochs, int
  * Runs epochs [start_epoch, start_epoch + epochs) of Algorithm 1 on Z in
  * place.  max_minibatches < 0 runs every minibatch of each epoch; otherwise
  * only the first max_minibatches of each epoch (used to time a bounded
- * sample of a large epoch).  walk > 0: rForce2Vec, N(u) from Algorithm 3
- * (orc_train is walk = 0).  Returns 0, or -1 if memory ran out.
+ * sample of a large epoch).  walk > 0: rForce2Vec, N(u) from Algorithm 3;
+ * shared != 0: one sample set S_b per minibatch (orc_train is neither).
+ * Returns 0, or -1 if memory ran out.
  */
-int orc_train_walk(int model, int64_t n, int32_t d,
-                   const int32_t *row_ptr, const int32_t *col_idx,
-                   double *Z, int32_t s, int32_t walk, int64_t b, uint64_t seed,
-                   double lr0, int32_t schedule, int32_t total_epochs,
-                   int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
-                   const int64_t *samp_ptr, const int32_t *samp_idx)
+int orc_train_ex(int model, int64_t n, int32_t d,
+                 const int32_t *row_ptr, const int32_t *col_idx,
+                 double *Z, int32_t s, int32_t walk, int32_t shared, int64_t b, uint64_t seed,
+                 double lr0, int32_t schedule, int32_t total_epochs,
+                 int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
+                 const int64_t *samp_ptr, const int32_t *samp_idx)
 {
     double *grad = (double *)malloc((size_t)b * (size_t)d * sizeof(double));
     if (!grad) return -1;
@@ -457,8 +473,8 @@ int orc_train_walk(int model, int64_t n, int32_t d,
             if (max_minibatches >= 0 && nmb >= max_minibatches) break;
             ++nmb;
             const int64_t u1 = (u0 + b < n) ? u0 + b : n;
-            orc_grad_minibatch_walk_abs(model, n, d, row_ptr, col_idx, Z, NULL, u0, u1, s, walk,
-                                        seed, e, samp_ptr, samp_idx, grad, NULL);
+            orc_grad_minibatch_ex(model, n, d, row_ptr, col_idx, Z, NULL, u0, u1, s, walk,
+                                  shared ? b : 0, seed, e, samp_ptr, samp_idx, grad, NULL);
             for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
                 for (int32_t j = 0; j < d; ++j) {
                     double z = Z[u * d + j] - eta * grad[(u - u0) * d + j];
@@ -481,9 +497,8 @@ int orc_train(int model, int64_t n, int32_t d,
               int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
               const int64_t *samp_ptr, const int32_t *samp_idx)
 {
-    return orc_train_walk(model, n, d, row_ptr, col_idx, Z, s, 0, b, seed, lr0, schedule,
-                          total_epochs, start_epoch, epochs, max_minibatches, samp_ptr,
-                          samp_idx);
+    return orc_train_ex(model, n, d, row_ptr, col_idx, Z, s, 0, 0, b, seed, lr0, schedule,
+                        total_epochs, start_epoch, epochs, max_minibatches, samp_ptr, samp_idx);
 }
 
 /* ------------------------------------------------------------------ */
