@@ -62,6 +62,8 @@ def parse():
                     help="force model (fr, linlog, forceatlas: single-graph workload only)")
     ap.add_argument("--walk", type=int, default=0,
                     help="rForce2Vec walk length (0: 1-hop neighbourhoods)")
+    ap.add_argument("--shared-samples", action="store_true",
+                    help="one negative-sample set per minibatch (Algorithm 1 line 6)")
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
@@ -96,6 +98,9 @@ def hbm_peak():
 
 def workload_config(g, args, d=128, s=5, b=4096):
     walk = f" rwalk{args.walk}" if args.walk else ""
+    walk += " shared-samples" if args.shared_samples else ""
+    if args.model != "tdist":
+        walk += f" {args.model}"
     return {
         "workload": f"force2vec-epoch rmat-scale{args.scale} holdout5% d{d} s{s} b{b}{walk}",
         "graph": f"R-MAT n=2^{args.scale}, 16*2^{args.scale} directed edges (a=.57,b=c=.19), "
@@ -104,6 +109,8 @@ def workload_config(g, args, d=128, s=5, b=4096):
         "force_model": args.model, "lr": "0.02 linearly decayed",
         "neighbourhood": (f"random walks of {args.walk} steps (Algorithm 3)" if args.walk
                           else "1-hop neighbours (Algorithm 2)"),
+        "negative_samples": ("one set of s per minibatch (Algorithm 1 line 6)"
+                             if args.shared_samples else "s per vertex"),
         "step": "one epoch (all minibatches)",
         "l2": "inputs larger than L2 (Z 2 x 512 MB FP32 double buffer, CSR 120 MB; L2 129 MB)",
     }
@@ -197,7 +204,8 @@ def vertex_pairs(g, s, walk):
     return (np.where(deg > 0, walk, 0) if walk else deg) + s
 
 
-def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None, walk=0):
+def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None, walk=0,
+                shared=False):
     """Times the FP64 oracle over the first minibatches of epoch 0 until about
     `budget_s` seconds of work; returns (pairs/s, pairs, minibatches, threads)."""
     import oracle
@@ -216,7 +224,7 @@ def oracle_rate(g, model, budget_s, d=128, s=5, b=4096, seed=1, max_mb=None, wal
         for k in range(done_mb, k1):
             a0, a1 = k * b, min(g.n, (k + 1) * b)
             G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0,
-                                      walk=walk)
+                                      walk=walk, shared_b=b if shared else 0)
             Z[a0:a1] -= 0.02 * G
         elapsed += time.perf_counter() - t0
         pairs += sub_pairs
@@ -242,7 +250,7 @@ def run_reference(args, g, world, rank):
         for k in range(k0, min(M, k0 + mb_per_step)):
             a0, a1 = k * b, min(g.n, (k + 1) * b)
             G = oracle.grad_minibatch(model, g.row_ptr, g.col_idx, Z, a0, a1, s, seed, 0,
-                                      walk=args.walk)
+                                      walk=args.walk, shared_b=b if args.shared_samples else 0)
             Z[a0:a1] -= 0.02 * G
             pairs += int(vp[a0:a1].sum())
         return pairs
@@ -284,10 +292,11 @@ def run_ours(args, g, world, rank, local):
     d, s, b, seed, lr = 128, 5, 4096, 1, 0.02
     model = MODEL_IDS[args.model]
     total_epochs = max(20, args.warmup + args.steps)
+    flags = f2v.FLAG_SHARED_SAMPLES if args.shared_samples else 0
 
     def make(m):
         ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=m, s=s, lr=lr, minibatch=b,
-                          seed=seed, stream=stream, walk_length=args.walk)
+                          seed=seed, stream=stream, walk_length=args.walk, flags=flags)
         ctx.set_schedule(f2v.LR_LINEAR, total_epochs)
         return ctx
 
@@ -331,7 +340,7 @@ def run_ours(args, g, world, rank, local):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if (tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.scale
-                and not args.walk):
+                and not args.walk and not args.shared_samples and args.model == "tdist"):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -378,7 +387,8 @@ def run_ours(args, g, world, rank, local):
 
         def job():
             with f2v.Context(rp.numpy(), ci.numpy(), g.n, d, model=model, s=s, lr=lr,
-                             minibatch=b, seed=seed, stream=stream, walk_length=args.walk) as c:
+                             minibatch=b, seed=seed, stream=stream, walk_length=args.walk,
+                             flags=flags) as c:
                 c.set_schedule(f2v.LR_LINEAR, job_epochs)
                 c.train(job_epochs)
                 c.embedding_into_host(zout.numpy())
@@ -399,7 +409,8 @@ def run_ours(args, g, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds, walk=args.walk)
+        rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds, walk=args.walk,
+                                                    shared=args.shared_samples)
         cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "kind": "oracle",
                "sample": f"first {mbs} minibatches (b=4096) of epoch 0, {pairs} pairs, FP64, "
                          f"{el:.1f} s"}

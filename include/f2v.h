@@ -94,6 +94,14 @@ typedef enum { F2V_LR_CONSTANT = 0, F2V_LR_LINEAR = 1 } f2v_schedule;
 #define F2V_FLAG_CHECK_SYMMETRY 0x1u   /* reject a CSR that is not symmetric */
 #define F2V_FLAG_NO_STAGING 0x2u       /* use the register-gather kernel even where
                                           the shared-memory staged one exists */
+#define F2V_FLAG_SHARED_SAMPLES 0x4u   /* the literal Algorithm 1 line 6: one set S_b
+                                          of s negative samples per minibatch, used
+                                          by every vertex of it (sample j of
+                                          minibatch k in epoch e = Philox(key = seed,
+                                          ctr = (k, e, j, 2)).x0 mod n; a sample equal
+                                          to u adds no force).  Without it each vertex
+                                          u draws its own s samples, ctr = (u, e, j, 0)
+                                          (the O(nsd) cost of Sec. III-C). */
 
 /*
  * Creates a context for one graph on the current CUDA device: validates and

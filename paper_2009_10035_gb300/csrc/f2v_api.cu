@@ -78,14 +78,15 @@ __global__ void init_kernel(Ts *z, float *master, int64_t n, int d, uint32_t k0,
     }
 }
 
-__global__ void samples_kernel(int32_t *out, int64_t n, int s, uint32_t epoch, uint32_t k0,
-                               uint32_t k1)
+__global__ void samples_kernel(int32_t *out, int64_t n, int s, int32_t shared_b, uint32_t epoch,
+                               uint32_t k0, uint32_t k1)
 {
     const int64_t total = n * (int64_t)s;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = (uint32_t)(t / s), k = (uint32_t)(t % s);
-        out[t] = (int32_t)(philox_x0(u, epoch, k, 0u, k0, k1) % (uint32_t)n);
+        const int64_t u = t / s;
+        const uint32_t k = (uint32_t)(t % s);
+        out[t] = (int32_t)negative_sample(u, epoch, k, shared_b, (int32_t)n, k0, k1);
     }
 }
 
@@ -112,6 +113,7 @@ struct f2v_ctx {
     int device = 0;
     int n = 0, d = 0, ld = 0, s = 0, b = 0;
     int walk = 0;                          // rForce2Vec walk length (0: neighbours, Alg. 2)
+    bool shared = false;                   // one sample set S_b per minibatch (Alg. 1 line 6)
     int64_t nnz = 0;
     int64_t pairs = 0;                     // force pairs per epoch
     int model = 0;
@@ -406,17 +408,19 @@ int num_minibatches(const f2v_ctx *c) { return (c->n + c->b - 1) / c->b; }
 // The staged kernel reads every pair's partner from an expanded list, and
 // so does the register kernel in the rForce2Vec form (walks are drawn once
 // per epoch into the list).
-bool uses_partner_list(const f2v_ctx *c) { return c->bulk || c->walk > 0; }
+bool uses_partner_list(const f2v_ctx *c) { return c->bulk || c->walk > 0 || c->shared; }
 
 cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st)
 {
     c->launches++;
+    const int32_t shared_b = c->shared ? c->b : 0;
     if (c->walk > 0)
         return launch_expand_walks(c->row_ptr, c->col_idx, c->apair, c->n, c->s, c->walk,
-                                   (uint32_t)epoch, (uint32_t)c->seed,
+                                   shared_b, (uint32_t)epoch, (uint32_t)c->seed,
                                    (uint32_t)(c->seed >> 32), buf, st);
-    return launch_expand_partners(c->row_ptr, c->col_idx, c->apair, c->n, c->s, (uint32_t)epoch,
-                                  (uint32_t)c->seed, (uint32_t)(c->seed >> 32), buf, st);
+    return launch_expand_partners(c->row_ptr, c->col_idx, c->apair, c->n, c->s, shared_b,
+                                  (uint32_t)epoch, (uint32_t)c->seed, (uint32_t)(c->seed >> 32),
+                                  buf, st);
 }
 
 // Reads (and clears) the device error word after the stream has drained.
@@ -464,7 +468,7 @@ void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
     a.eta = eta;
     a.model = c->model;
     a.err = c->err_word;
-    a.partner = (c->walk > 0) ? c->partner_buf[c->epoch & 1] : nullptr;
+    a.partner = (c->walk > 0 || c->shared) ? c->partner_buf[c->epoch & 1] : nullptr;
 }
 
 template <typename Ts>
@@ -678,6 +682,7 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
     }
     c->n = n; c->d = d; c->ld = d; c->s = s; c->b = minibatch; c->model = (int)model;
     c->walk = walk;
+    c->shared = (flags & F2V_FLAG_SHARED_SAMPLES) != 0;
     c->precision = precision; c->seed = seed; c->lr = lr;
     c->stream = (cudaStream_t)stream;
     c->nnz = row_ptr[n];
@@ -1056,7 +1061,8 @@ f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t c
     cudaError_t e = cudaMallocAsync((void **)&dbuf, want * sizeof(int32_t), ctx->stream);
     if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "debug_samples: %s", cudaGetErrorString(e));
     const int blocks = (int)std::min<int64_t>(((int64_t)want + 255) / 256, 152 * 16);
-    samples_kernel<<<blocks, 256, 0, ctx->stream>>>(dbuf, ctx->n, ctx->s, (uint32_t)epoch,
+    samples_kernel<<<blocks, 256, 0, ctx->stream>>>(dbuf, ctx->n, ctx->s,
+                                                     ctx->shared ? ctx->b : 0, (uint32_t)epoch,
                                                      (uint32_t)ctx->seed,
                                                      (uint32_t)(ctx->seed >> 32));
     ctx->launches++;

@@ -34,6 +34,20 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
 // Z0[i][j] = (Philox(ctr=(i, j, 0xFFFF, 0)).x0 >> 8) * 2^-24 - 0.5: a multiple
 // of 2^-24 in [-0.5, 0.5), exact in FP32 (the initial embedding, uniform as
 // the paper's random start).
+// Negative sample k of vertex u in epoch `epoch`: its own draw
+// Philox(ctr = (u, epoch, k, 0)).x0 mod n, or, with shared_b > 0 (one set S_b
+// per minibatch, the literal Alg. 1 line 6), the draw of u's minibatch
+// Philox(ctr = (u / shared_b, epoch, k, 2)).x0 mod n.
+__device__ __forceinline__ uint32_t negative_sample(int64_t u, uint32_t epoch, uint32_t k,
+                                                    int32_t shared_b, int32_t n, uint32_t key0,
+                                                    uint32_t key1)
+{
+    const uint32_t x = (shared_b > 0)
+                           ? philox_x0((uint32_t)(u / shared_b), epoch, k, 2u, key0, key1)
+                           : philox_x0((uint32_t)u, epoch, k, 0u, key0, key1);
+    return x % (uint32_t)n;
+}
+
 __device__ __forceinline__ float z0_value(uint32_t i, uint32_t j, uint32_t k0, uint32_t k1)
 {
     const uint32_t x = philox_x0(i, j, 0xFFFFu, 0u, k0, k1);

@@ -7,7 +7,8 @@
 // tile's partners with one coalesced load, instead of a dependent chain
 // (row pointers, then column indices) and a Philox evaluation per sample.
 // Samples follow the same counter layout as everywhere else:
-// w = Philox4x32-10(key, ctr = (u, epoch, k, 0)).x0 mod n.
+// w = Philox4x32-10(key, ctr = (u, epoch, k, 0)).x0 mod n, or with shared
+// samples (one set S_b per minibatch k = u / b) ctr = (k, epoch, j, 2).
 // rForce2Vec (Algorithm 3) replaces the neighbours of u by the walk-length
 // steps of a random walk from u (none if u has no neighbours); step i draws
 // ctr = (u, epoch, i, 1), moves to that neighbour of the current vertex, and
@@ -27,8 +28,8 @@ namespace {
 __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
                                        const int32_t *__restrict__ col_idx,
                                        const int64_t *__restrict__ apair, int32_t n, int32_t s,
-                                       uint32_t epoch, uint32_t key0, uint32_t key1,
-                                       int32_t *__restrict__ partner)
+                                       int32_t shared_b, uint32_t epoch, uint32_t key0,
+                                       uint32_t key1, int32_t *__restrict__ partner)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -39,8 +40,7 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
         const int32_t deg = row_ptr[u + 1] - r0;
         for (int32_t j = lane; j < deg; j += 32) partner[base + j] = col_idx[r0 + j];
         for (int32_t k = lane; k < s; k += 32) {
-            const uint32_t w = philox_x0((uint32_t)u, epoch, (uint32_t)k, 0u, key0, key1) %
-                               (uint32_t)n;
+            const uint32_t w = negative_sample(u, epoch, (uint32_t)k, shared_b, n, key0, key1);
             partner[base + deg + k] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
         }
         if (deg + s == 0 && lane == 0) partner[base] = kPartnerNone;   // the empty pair
@@ -53,8 +53,8 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
 __global__ void expand_walks_kernel(const int32_t *__restrict__ row_ptr,
                                     const int32_t *__restrict__ col_idx,
                                     const int64_t *__restrict__ apair, int32_t n, int32_t s,
-                                    int32_t walk, uint32_t epoch, uint32_t key0, uint32_t key1,
-                                    int32_t *__restrict__ partner)
+                                    int32_t walk, int32_t shared_b, uint32_t epoch, uint32_t key0,
+                                    uint32_t key1, int32_t *__restrict__ partner)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += stride) {
@@ -81,8 +81,7 @@ __global__ void expand_walks_kernel(const int32_t *__restrict__ row_ptr,
             }
         }
         for (int32_t k = 0; k < s; ++k) {
-            const uint32_t w = philox_x0((uint32_t)u, epoch, (uint32_t)k, 0u, key0, key1) %
-                               (uint32_t)n;
+            const uint32_t w = negative_sample(u, epoch, (uint32_t)k, shared_b, n, key0, key1);
             partner[p++] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
         }
         if (!has_walk && s == 0) partner[p] = kPartnerNone;   // the empty pair
@@ -114,11 +113,11 @@ int grid_for(int64_t threads)
 
 cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
                                 const int64_t *apair, int32_t n, int32_t s, int32_t walk,
-                                uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
-                                cudaStream_t st)
+                                int32_t shared_b, uint32_t epoch, uint32_t key0, uint32_t key1,
+                                int32_t *partner, cudaStream_t st)
 {
-    expand_walks_kernel<<<grid_for(n), 256, 0, st>>>(row_ptr, col_idx, apair, n, s, walk, epoch,
-                                                     key0, key1, partner);
+    expand_walks_kernel<<<grid_for(n), 256, 0, st>>>(row_ptr, col_idx, apair, n, s, walk,
+                                                     shared_b, epoch, key0, key1, partner);
     return cudaGetLastError();
 }
 
@@ -132,8 +131,8 @@ cudaError_t launch_extract_walks(const int64_t *apair, const int32_t *row_ptr, i
 }
 
 cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
-                                   const int64_t *apair, int32_t n, int32_t s, uint32_t epoch,
-                                   uint32_t key0, uint32_t key1, int32_t *partner,
+                                   const int64_t *apair, int32_t n, int32_t s, int32_t shared_b,
+                                   uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st)
 {
     int dev = 0, sms = 0;
@@ -142,8 +141,8 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
     const int64_t warps_needed = n;
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)std::max(sms, 1) * 16));
-    expand_partners_kernel<<<blocks, 256, 0, st>>>(row_ptr, col_idx, apair, n, s, epoch, key0,
-                                                   key1, partner);
+    expand_partners_kernel<<<blocks, 256, 0, st>>>(row_ptr, col_idx, apair, n, s, shared_b,
+                                                   epoch, key0, key1, partner);
     return cudaGetLastError();
 }
 

@@ -107,10 +107,11 @@ bool make_row_map(CUtensorMap *map, void *base, int64_t rows, int d, bool bf16,
 constexpr int32_t kPartnerNone = -1;
 
 // Writes the partner code of every pair of epoch `epoch` (pair apair[u] + j
-// of vertex u), one warp per vertex.
+// of vertex u), one warp per vertex.  shared_b > 0: the samples are the
+// shared set of u's minibatch of that size (negative_sample).
 cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
-                                   const int64_t *apair, int32_t n, int32_t s, uint32_t epoch,
-                                   uint32_t key0, uint32_t key1, int32_t *partner,
+                                   const int64_t *apair, int32_t n, int32_t s, int32_t shared_b,
+                                   uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st);
 
 // rForce2Vec (Algorithm 3): the same list with vertex u's first `walk` pairs
@@ -119,8 +120,8 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
 // Philox(key, ctr = (u, epoch, i, 1)).x0 mod deg(w).
 cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
                                 const int64_t *apair, int32_t n, int32_t s, int32_t walk,
-                                uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
-                                cudaStream_t st);
+                                int32_t shared_b, uint32_t epoch, uint32_t key0, uint32_t key1,
+                                int32_t *partner, cudaStream_t st);
 
 // out[u * walk + i]: the code of walk step i of vertex u in the list
 // `partner` (kPartnerNone for a vertex without neighbours).

@@ -70,6 +70,7 @@ def bf16_round(x):
 
 def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedule=None,
                 total_epochs=0, precision=f2v.FP32, tol=TOL_STEP, flags=0, walk=0):
+    shared_b = b if flags & f2v.FLAG_SHARED_SAMPLES else 0
     """Minibatch by minibatch: the oracle computes each checked minibatch's
     update (Algorithm 2 + Eq. 10) from the GPU's own Z before it, so that each
     kernel launch is compared in isolation.  Error bound: FP32 accumulation of
@@ -93,7 +94,8 @@ def check_steps(g, d, model, s, b, lr=0.02, seed=1, epochs=1, steps=None, schedu
                 u0, u1 = k * b, min(g.n, (k + 1) * b)
                 gather = bf16_round(before) if precision == f2v.BF16 else None
                 G, A = oracle.grad_minibatch_abs(model, g.row_ptr, g.col_idx, before, u0, u1,
-                                                 s, seed, e, gather=gather, walk=walk)
+                                                 s, seed, e, gather=gather, walk=walk,
+                                                 shared_b=shared_b)
                 eta = oracle.learning_rate(lr, 0 if schedule is None else schedule,
                                            total_epochs, e)
                 want = before[u0:u1] - eta * G
@@ -557,3 +559,58 @@ def test_rmat_scale20_d128_other_models(model, rmat20):
     worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps,
                         schedule=f2v.LR_LINEAR, total_epochs=20)
     print(f"rmat20 model={model}: worst scaled error {worst:.3e}")
+
+
+# ---------------------------------------------------------------- shared samples (Alg. 1 line 6)
+
+@pytest.mark.parametrize("b", [1, 100, 256])
+def test_shared_samples_bit_exact(b):
+    g = graphs.erdos_renyi(1000, p=0.01, seed=2)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, s=5, minibatch=b, seed=17,
+                     flags=f2v.FLAG_SHARED_SAMPLES) as ctx:
+        for epoch in (0, 5):
+            np.testing.assert_array_equal(ctx.debug_samples(epoch),
+                                          oracle.samples_shared(g.n, 5, b, epoch, 17))
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [4, 32, 128])
+def test_shared_samples_steps(model, d):
+    """Every vertex of a minibatch repelled by the same s samples: register
+    kernel (d = 4, 32) and staged kernel (d = 128)."""
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, d, model, 5, 256, lr=0.05, seed=4, epochs=2,
+                steps={(0, 0), (0, 3), (1, 2), (1, 5)}, flags=f2v.FLAG_SHARED_SAMPLES)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_shared_samples_with_walks_and_bf16(model):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_steps(g, 128, model, 5, 256, lr=0.05, seed=4, epochs=1, steps={(0, 1)},
+                flags=f2v.FLAG_SHARED_SAMPLES, walk=5)
+    check_steps(g, 128, model, 5, 256, lr=0.05, seed=4, epochs=1, steps={(0, 2)},
+                flags=f2v.FLAG_SHARED_SAMPLES, precision=f2v.BF16)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_shared_samples_one_epoch(model):
+    g = graphs.config1_graph()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, lr=0.02, minibatch=256,
+                     seed=1, flags=f2v.FLAG_SHARED_SAMPLES) as ctx:
+        ctx.epoch()
+        got = ctx.embedding()
+    Z0 = oracle.init_embedding(g.n, 32, 1)
+    want = oracle.train(model, g.row_ptr, g.col_idx, Z0, 5, 256, 1, 0.02, 1, shared=True)
+    err = rel_err(got, want)
+    assert err.max() <= TOL_1EPOCH, float(err.max())
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_rmat_scale20_d128_shared_samples(model, rmat20):
+    g = rmat20
+    b = 4096
+    M = -(-g.n // b)
+    steps = {(0, 0), (0, M // 2 + 1), (0, M - 1)}
+    worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps,
+                        flags=f2v.FLAG_SHARED_SAMPLES, schedule=f2v.LR_LINEAR, total_epochs=20)
+    print(f"rmat20 shared samples model={model}: worst scaled error {worst:.3e}")
