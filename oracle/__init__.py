@@ -16,6 +16,7 @@ Every function cites the passage it follows:
   init_embedding  Sec. III-C "Initialization": random Z, uniform [-0.5, 0.5)
   samples         negative samples, s per vertex (Sec. III-C complexity text)
   samples_shared  the literal Alg. 1 line 6: one set S_b per minibatch
+  partition       the literal Alg. 1 line 3: a random partition per epoch
   grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t),
                   Table "diffmodels" (FR, LinLog, ForceAtlas)
   walk            Algorithm 3 (GenWalk), the rForce2Vec neighbourhood
@@ -97,8 +98,13 @@ def _load():
         lib.orc_sample_shared.restype = u32
         lib.orc_walk.argtypes = [u64, vp, vp, i64, i32, i32, vp]
         lib.orc_walk.restype = None
-        lib.orc_train_ex.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i32, i32, i64,
-                                     u64, f64, i32, i32, i32, i32, i64, vp, vp]
+        lib.orc_train_ex.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, i32, i32, i32, i32,
+                                     i64, u64, f64, i32, i32, i32, i32, i64, vp, vp]
+        lib.orc_grad_core.argtypes = [ctypes.c_int, i64, i32, vp, vp, vp, vp, vp, i64, i64, i32,
+                                      i32, i64, i64, u64, i32, vp, vp, vp, vp]
+        lib.orc_grad_core.restype = None
+        lib.orc_partition.argtypes = [u64, i64, i32, vp]
+        lib.orc_partition.restype = ctypes.c_int
         lib.orc_train_ex.restype = ctypes.c_int
         lib.orc_learning_rate.argtypes = [f64, i32, i32, i32]
         lib.orc_learning_rate.restype = f64
@@ -229,24 +235,56 @@ def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoc
     return g, ga
 
 
+def partition(n: int, epoch: int, seed: int) -> np.ndarray:
+    """The random partition of an epoch (Alg. 1 line 3): the vertices in
+    minibatch order; minibatch k is positions [k b, (k+1) b)."""
+    lib = _load()
+    perm = np.zeros(max(n, 1), dtype=np.int64)
+    if lib.orc_partition(seed, n, epoch, _ptr(perm)) != 0:
+        raise MemoryError("oracle partition: out of memory")
+    return perm[:n]
+
+
+def grad_vertices_abs(model, row_ptr, col_idx, Z, verts, s, seed, epoch, gather=None, walk=0,
+                      shared_k=-1):
+    """Algorithm 2 for the vertex list `verts` (one minibatch of a random
+    partition): returns (grad, grad_abs), rows in list order.  shared_k >= 0:
+    the shared sample set of minibatch shared_k."""
+    lib = _load()
+    row_ptr, col_idx = _csr(row_ptr, col_idx)
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    n, d = Z.shape
+    Zp = None if gather is None else np.ascontiguousarray(gather, dtype=np.float64)
+    v = np.ascontiguousarray(verts, dtype=np.int64)
+    g = np.zeros((v.size, d), dtype=np.float64)
+    ga = np.zeros((v.size, d), dtype=np.float64)
+    if v.size:
+        lib.orc_grad_core(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z),
+                          None if Zp is None else _ptr(Zp), _ptr(v), 0, v.size, s, int(walk),
+                          int(shared_k), 0, seed, epoch, None, None, _ptr(g), _ptr(ga))
+    return g, ga
+
+
 def learning_rate(lr0: float, schedule: int, total_epochs: int, epoch: int) -> float:
     return _load().orc_learning_rate(lr0, schedule, total_epochs, epoch)
 
 
 def train(model, row_ptr, col_idx, Z, s, b, seed, lr, epochs, start_epoch=0,
           schedule=0, total_epochs=0, max_minibatches=-1, injected=None,
-          walk=0, shared=False) -> np.ndarray:
+          walk=0, shared=False, partition=False) -> np.ndarray:
     """Algorithm 1 from embedding Z (copied); returns the new FP64 embedding.
     walk > 0: rForce2Vec, N(u) from Algorithm 3 with walks of that length.
-    shared: one sample set S_b per minibatch (the literal line 6)."""
+    shared: one sample set S_b per minibatch (the literal line 6).
+    partition: a new random partition every epoch (the literal line 3)."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.array(Z, dtype=np.float64, order="C", copy=True)
     n, d = Z.shape
     sp, si = _injected(injected)
     rc = lib.orc_train_ex(model, n, d, _ptr(row_ptr), _ptr(col_idx), _ptr(Z), s, int(walk),
-                          int(bool(shared)), b, seed, lr, schedule, total_epochs, start_epoch,
-                          epochs, max_minibatches, _ptr(sp), _ptr(si))
+                          int(bool(shared)), int(bool(partition)), b, seed, lr, schedule,
+                          total_epochs, start_epoch, epochs, max_minibatches, _ptr(sp),
+                          _ptr(si))
     if rc != 0:
         raise MemoryError("oracle train: out of memory")
     return Z

@@ -38,7 +38,12 @@
  *   - Synchronous minibatch SGD (Sec. III-B): every gradient of a minibatch is
  *     computed from Z as it stood when the minibatch began; the minibatch's
  *     rows are then updated; the next minibatch sees those updates.
- *   - Minibatch k holds vertex ids [k*b, min((k+1)*b, n)) in id order.
+ *   - Minibatch k holds vertex ids [k*b, min((k+1)*b, n)) in id order; or,
+ *     as an option, the positions [k*b, min((k+1)*b, n)) of a random
+ *     permutation drawn anew each epoch (Alg. 1 line 3, "randomly without
+ *     replacement"): vertices sorted by Philox(key, ctr=(v, e, 0, 3)).x0,
+ *     ties by id (orc_partition).  Shared samples then belong to the
+ *     minibatch index k.
  *   - Only z_u for u in the minibatch is updated (Algorithm 1, lines 8-9).
  *   - Negative sample k of vertex u in epoch e is
  *       w = Philox(key=(seed lo, seed hi), ctr=(u, e, k, 0)).x0 mod n,
@@ -362,31 +367,37 @@ static void repulsive_grad(int model, const double *zu, const double *zw, int32_
  * storage form that keeps partner rows in reduced precision beside a full
  * precision copy of each vertex's own row.
  */
-/* walk > 0: N(u) is the walk of Algorithm 3 (rForce2Vec) instead of the
-   neighbours of u.  shared_b > 0: the samples of u are the set S_b of its
-   minibatch k = u / shared_b (orc_sample_shared) instead of its own. */
-void orc_grad_minibatch_ex(int model, int64_t n, int32_t d,
-                           const int32_t *row_ptr, const int32_t *col_idx,
-                           const double *Z, const double *Zp, int64_t u_begin,
-                           int64_t u_end, int32_t s, int32_t walk, int64_t shared_b,
-                           uint64_t seed, int32_t epoch, const int64_t *samp_ptr,
-                           const int32_t *samp_idx, double *grad, double *grad_abs)
+/*
+ * Algorithm 2 for the `count` vertices vlist[0..count) (vlist == NULL: the
+ * range u_begin, u_begin + 1, ...); row i of grad is vertex i's gradient.
+ * walk > 0: N(u) is the walk of Algorithm 3 (rForce2Vec) instead of the
+ * neighbours of u.  shared_k >= 0: the samples are the shared set S_b of
+ * minibatch shared_k (orc_sample_shared) instead of u's own; shared_k ==
+ * -2: the shared set of minibatch u / shared_b.
+ */
+void orc_grad_core(int model, int64_t n, int32_t d, const int32_t *row_ptr,
+                   const int32_t *col_idx, const double *Z, const double *Zp,
+                   const int64_t *vlist, int64_t u_begin, int64_t count, int32_t s, int32_t walk,
+                   int64_t shared_k, int64_t shared_b, uint64_t seed, int32_t epoch,
+                   const int64_t *samp_ptr, const int32_t *samp_idx, double *grad,
+                   double *grad_abs)
 {
     if (Zp == NULL) Zp = Z;
     #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t u = u_begin; u < u_end; ++u) {
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t u = vlist ? vlist[i] : u_begin + i;
         const double *zu = Z + u * d;
         double ga[d], gr[d];            /* grad f_a(u), grad f_r(u) */
-        double *gabs = grad_abs ? grad_abs + (u - u_begin) * d : NULL;
+        double *gabs = grad_abs ? grad_abs + i * d : NULL;
         memset(ga, 0, sizeof ga);
         memset(gr, 0, sizeof gr);
         if (gabs) memset(gabs, 0, sizeof(double) * (size_t)d);
         if (walk > 0) {
             int32_t nw[walk];
             orc_walk(seed, row_ptr, col_idx, u, epoch, walk, nw);
-            for (int32_t i = 0; i < walk; ++i) {
-                if (nw[i] < 0 || nw[i] == u) continue;
-                attractive_grad(model, zu, Zp + (int64_t)nw[i] * d, d, ga, gabs);
+            for (int32_t j = 0; j < walk; ++j) {
+                if (nw[j] < 0 || nw[j] == u) continue;
+                attractive_grad(model, zu, Zp + (int64_t)nw[j] * d, d, ga, gabs);
             }
         } else {
             for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
@@ -395,12 +406,13 @@ void orc_grad_minibatch_ex(int model, int64_t n, int32_t d,
             }
         }
         if (samp_ptr == NULL) {
+            const int64_t kb = (shared_k == -2) ? u / shared_b : shared_k;
             for (int32_t k = 0; k < s; ++k) {
                 const int64_t w =
-                    shared_b > 0 ? orc_sample_shared(seed, (uint32_t)(u / shared_b),
-                                                     (uint32_t)epoch, (uint32_t)k, (uint32_t)n)
-                                 : orc_sample(seed, (uint32_t)u, (uint32_t)epoch, (uint32_t)k,
-                                              (uint32_t)n);
+                    kb >= 0 ? orc_sample_shared(seed, (uint32_t)kb, (uint32_t)epoch, (uint32_t)k,
+                                                (uint32_t)n)
+                            : orc_sample(seed, (uint32_t)u, (uint32_t)epoch, (uint32_t)k,
+                                         (uint32_t)n);
                 if (w == u) continue;
                 repulsive_grad(model, zu, Zp + w * d, d, gr, gabs);
             }
@@ -411,9 +423,24 @@ void orc_grad_minibatch_ex(int model, int64_t n, int32_t d,
                 repulsive_grad(model, zu, Zp + w * d, d, gr, gabs);
             }
         }
-        double *gu = grad + (u - u_begin) * d;
+        double *gu = grad + i * d;
         for (int32_t j = 0; j < d; ++j) gu[j] = ga[j] + gr[j];
     }
+}
+
+/* walk > 0: N(u) is the walk of Algorithm 3 (rForce2Vec) instead of the
+   neighbours of u.  shared_b > 0: the samples of u are the set S_b of its
+   minibatch k = u / shared_b (orc_sample_shared) instead of its own. */
+void orc_grad_minibatch_ex(int model, int64_t n, int32_t d,
+                           const int32_t *row_ptr, const int32_t *col_idx,
+                           const double *Z, const double *Zp, int64_t u_begin,
+                           int64_t u_end, int32_t s, int32_t walk, int64_t shared_b,
+                           uint64_t seed, int32_t epoch, const int64_t *samp_ptr,
+                           const int32_t *samp_idx, double *grad, double *grad_abs)
+{
+    orc_grad_core(model, n, d, row_ptr, col_idx, Z, Zp, NULL, u_begin, u_end - u_begin, s,
+                  walk, shared_b > 0 ? -2 : -1, shared_b, seed, epoch, samp_ptr, samp_idx, grad,
+                  grad_abs);
 }
 
 void orc_grad_minibatch_abs(int model, int64_t n, int32_t d,
@@ -442,6 +469,38 @@ void orc_grad_minibatch(int model, int64_t n, int32_t d,
 /* Algorithm 1                                                          */
 /* ------------------------------------------------------------------ */
 
+/*
+ * The random partition of epoch e (Alg. 1 line 3, "randomly without
+ * replacement"): perm lists the vertices in increasing order of the key
+ * Philox(key, ctr=(v, e, 0, 3)).x0, ties by id; minibatch k is
+ * perm[k b .. min((k+1) b, n)).
+ */
+typedef struct {
+    uint32_t key;
+    int64_t v;
+} orc_keyed;
+
+static int cmp_keyed(const void *a, const void *b)
+{
+    const orc_keyed *x = (const orc_keyed *)a, *y = (const orc_keyed *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+int orc_partition(uint64_t seed, int64_t n, int32_t epoch, int64_t *perm)
+{
+    orc_keyed *t = (orc_keyed *)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_keyed));
+    if (!t) return -1;
+    for (int64_t v = 0; v < n; ++v) {
+        t[v].key = philox_x0(seed, (uint32_t)v, (uint32_t)epoch, 0u, 3u);
+        t[v].v = v;
+    }
+    qsort(t, (size_t)n, sizeof(orc_keyed), cmp_keyed);
+    for (int64_t i = 0; i < n; ++i) perm[i] = t[i].v;
+    free(t);
+    return 0;
+}
+
 double orc_learning_rate(double lr0, int32_t schedule, int32_t total_epochs, int32_t epoch)
 {
     if (schedule == 1 && total_epochs > 0)
@@ -454,30 +513,48 @@ double orc_learning_rate(double lr0, int32_t schedule, int32_t total_epochs, int
  * place.  max_minibatches < 0 runs every minibatch of each epoch; otherwise
  * only the first max_minibatches of each epoch (used to time a bounded
  * sample of a large epoch).  walk > 0: rForce2Vec, N(u) from Algorithm 3;
- * shared != 0: one sample set S_b per minibatch (orc_train is neither).
+ * shared != 0: one sample set S_b per minibatch; partition != 0: a new
+ * random partition every epoch (orc_partition) instead of the id ranges
+ * [k b, (k+1) b) (orc_train is none of these).
  * Returns 0, or -1 if memory ran out.
  */
 int orc_train_ex(int model, int64_t n, int32_t d,
                  const int32_t *row_ptr, const int32_t *col_idx,
-                 double *Z, int32_t s, int32_t walk, int32_t shared, int64_t b, uint64_t seed,
-                 double lr0, int32_t schedule, int32_t total_epochs,
+                 double *Z, int32_t s, int32_t walk, int32_t shared, int32_t partition,
+                 int64_t b, uint64_t seed, double lr0, int32_t schedule, int32_t total_epochs,
                  int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
                  const int64_t *samp_ptr, const int32_t *samp_idx)
 {
     double *grad = (double *)malloc((size_t)b * (size_t)d * sizeof(double));
-    if (!grad) return -1;
+    int64_t *perm = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!grad || !perm) {
+        free(grad);
+        free(perm);
+        return -1;
+    }
     for (int32_t e = start_epoch; e < start_epoch + epochs; ++e) {
         const double eta = orc_learning_rate(lr0, schedule, total_epochs, e);
+        /* line 3: the minibatches of this epoch */
+        if (partition) {
+            if (orc_partition(seed, n, e, perm) != 0) {
+                free(grad);
+                free(perm);
+                return -1;
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i) perm[i] = i;
+        }
         int64_t nmb = 0;
-        for (int64_t u0 = 0; u0 < n; u0 += b) {          /* each minibatch V_b */
+        for (int64_t p0 = 0; p0 < n; p0 += b) {          /* each minibatch V_b */
             if (max_minibatches >= 0 && nmb >= max_minibatches) break;
-            ++nmb;
-            const int64_t u1 = (u0 + b < n) ? u0 + b : n;
-            orc_grad_minibatch_ex(model, n, d, row_ptr, col_idx, Z, NULL, u0, u1, s, walk,
-                                  shared ? b : 0, seed, e, samp_ptr, samp_idx, grad, NULL);
-            for (int64_t u = u0; u < u1; ++u)            /* Eq. 10 */
+            const int64_t k = nmb++;
+            const int64_t p1 = (p0 + b < n) ? p0 + b : n;
+            orc_grad_core(model, n, d, row_ptr, col_idx, Z, NULL, perm + p0, 0, p1 - p0, s,
+                          walk, shared ? k : -1, b, seed, e, samp_ptr, samp_idx, grad, NULL);
+            for (int64_t i = p0; i < p1; ++i)            /* Eq. 10 */
                 for (int32_t j = 0; j < d; ++j) {
-                    double z = Z[u * d + j] - eta * grad[(u - u0) * d + j];
+                    const int64_t u = perm[i];
+                    double z = Z[u * d + j] - eta * grad[(i - p0) * d + j];
                     if (model != ORC_TDIST) {                /* bounded coordinates */
                         if (z > ORC_SIGMOID_BOUND) z = ORC_SIGMOID_BOUND;
                         if (z < -ORC_SIGMOID_BOUND) z = -ORC_SIGMOID_BOUND;
@@ -487,6 +564,7 @@ int orc_train_ex(int model, int64_t n, int32_t d,
         }
     }
     free(grad);
+    free(perm);
     return 0;
 }
 
@@ -497,7 +575,7 @@ int orc_train(int model, int64_t n, int32_t d,
               int32_t start_epoch, int32_t epochs, int64_t max_minibatches,
               const int64_t *samp_ptr, const int32_t *samp_idx)
 {
-    return orc_train_ex(model, n, d, row_ptr, col_idx, Z, s, 0, 0, b, seed, lr0, schedule,
+    return orc_train_ex(model, n, d, row_ptr, col_idx, Z, s, 0, 0, 0, b, seed, lr0, schedule,
                         total_epochs, start_epoch, epochs, max_minibatches, samp_ptr, samp_idx);
 }
 
