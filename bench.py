@@ -64,6 +64,8 @@ def parse():
                     help="rForce2Vec walk length (0: 1-hop neighbourhoods)")
     ap.add_argument("--shared-samples", action="store_true",
                     help="one negative-sample set per minibatch (Algorithm 1 line 6)")
+    ap.add_argument("--random-partition", action="store_true",
+                    help="a new random partition into minibatches every epoch (Algorithm 1 line 3)")
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
@@ -99,6 +101,7 @@ def hbm_peak():
 def workload_config(g, args, d=128, s=5, b=4096):
     walk = f" rwalk{args.walk}" if args.walk else ""
     walk += " shared-samples" if args.shared_samples else ""
+    walk += " random-partition" if args.random_partition else ""
     if args.model != "tdist":
         walk += f" {args.model}"
     return {
@@ -111,6 +114,8 @@ def workload_config(g, args, d=128, s=5, b=4096):
                           else "1-hop neighbours (Algorithm 2)"),
         "negative_samples": ("one set of s per minibatch (Algorithm 1 line 6)"
                              if args.shared_samples else "s per vertex"),
+        "minibatches": ("a new random partition every epoch (Algorithm 1 line 3)"
+                        if args.random_partition else "id ranges [k b, (k+1) b)"),
         "step": "one epoch (all minibatches)",
         "l2": "inputs larger than L2 (Z 2 x 512 MB FP32 double buffer, CSR 120 MB; L2 129 MB)",
     }
@@ -292,7 +297,8 @@ def run_ours(args, g, world, rank, local):
     d, s, b, seed, lr = 128, 5, 4096, 1, 0.02
     model = MODEL_IDS[args.model]
     total_epochs = max(20, args.warmup + args.steps)
-    flags = f2v.FLAG_SHARED_SAMPLES if args.shared_samples else 0
+    flags = (f2v.FLAG_SHARED_SAMPLES if args.shared_samples else 0) | \
+        (f2v.FLAG_RANDOM_PARTITION if args.random_partition else 0)
 
     def make(m):
         ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=m, s=s, lr=lr, minibatch=b,
@@ -340,7 +346,8 @@ def run_ours(args, g, world, rank, local):
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if (tr.get("kernel_hash") == kernel_hash() and tr.get("workload") == args.scale
-                and not args.walk and not args.shared_samples and args.model == "tdist"):
+                and not args.walk and not args.shared_samples and not args.random_partition
+                and args.model == "tdist"):
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass

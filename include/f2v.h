@@ -102,6 +102,16 @@ typedef enum { F2V_LR_CONSTANT = 0, F2V_LR_LINEAR = 1 } f2v_schedule;
                                           to u adds no force).  Without it each vertex
                                           u draws its own s samples, ctr = (u, e, j, 0)
                                           (the O(nsd) cost of Sec. III-C). */
+#define F2V_FLAG_RANDOM_PARTITION 0x8u /* the literal Algorithm 1 line 3: a new random
+                                          partition of V every epoch.  Epoch e orders
+                                          the vertices by Philox(key = seed, ctr =
+                                          (v, e, 0, 3)).x0, ties by id; minibatch k is
+                                          positions [k b, (k+1) b) of that order.
+                                          Without it minibatch k is the ids
+                                          [k b, (k+1) b) in every epoch.  Needs
+                                          F2V_FP32.  Costs a sort, a relabelling of
+                                          the CSR and a gather and scatter of Z per
+                                          epoch. */
 
 /*
  * Creates a context for one graph on the current CUDA device: validates and

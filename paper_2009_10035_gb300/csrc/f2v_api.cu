@@ -78,15 +78,18 @@ __global__ void init_kernel(Ts *z, float *master, int64_t n, int d, uint32_t k0,
     }
 }
 
-__global__ void samples_kernel(int32_t *out, int64_t n, int s, int32_t shared_b, uint32_t epoch,
-                               uint32_t k0, uint32_t k1)
+// rank (may be null): positions of the vertices in the epoch's random
+// partition, which decide a vertex's minibatch for shared samples.
+__global__ void samples_kernel(int32_t *out, int64_t n, int s, int32_t shared_b,
+                               const int32_t *rank, uint32_t epoch, uint32_t k0, uint32_t k1)
 {
     const int64_t total = n * (int64_t)s;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = t / s;
         const uint32_t k = (uint32_t)(t % s);
-        out[t] = (int32_t)negative_sample(u, epoch, k, shared_b, (int32_t)n, k0, k1);
+        const int64_t kb = shared_b > 0 ? (rank ? rank[u] : u) / shared_b : -1;
+        out[t] = (int32_t)negative_sample(u, kb, epoch, k, (int32_t)n, k0, k1);
     }
 }
 
@@ -114,6 +117,7 @@ struct f2v_ctx {
     int n = 0, d = 0, ld = 0, s = 0, b = 0;
     int walk = 0;                          // rForce2Vec walk length (0: neighbours, Alg. 2)
     bool shared = false;                   // one sample set S_b per minibatch (Alg. 1 line 6)
+    bool partition = false;                // a new random partition every epoch (Alg. 1 line 3)
     int64_t nnz = 0;
     int64_t pairs = 0;                     // force pairs per epoch
     int model = 0;
@@ -133,13 +137,26 @@ struct f2v_ctx {
     std::vector<int64_t> h_apair;          // n + 1
     std::vector<int64_t> mb_item_base;     // M + 1
     std::vector<int32_t> mb_C;             // pairs per item (chunk) of each minibatch
+    std::vector<int64_t> mb_p0;            // M + 1: first pair of each minibatch (and the end)
     int64_t max_items = 0;
 
     // device buffers
     int32_t *err_word = nullptr;           // set by a device wait that timed out
+    // the graph the kernels walk (with a random partition, relabelled into
+    // the epoch's order) and the graph as given (the same arrays otherwise)
     int32_t *row_ptr = nullptr, *col_idx = nullptr, *item_u0 = nullptr, *counter = nullptr;
     int64_t *apair = nullptr;
-    void *z[2] = {nullptr, nullptr};       // float or bf16 rows
+    int32_t *row_ptr0 = nullptr, *col_idx0 = nullptr;
+    int64_t *apair0 = nullptr;
+    // Z: z[cur] holds it as of the epoch's start (rows in id order), z[cur ^ 1]
+    // receives the epoch's updates.  With a random partition, z[cur ^ 1] holds
+    // Z gathered into the epoch's order and z[2] the updates in that order,
+    // scattered back into z[cur] when the epoch ends.
+    void *z[3] = {nullptr, nullptr, nullptr};   // float or bf16 rows
+    int32_t *perm = nullptr, *rank = nullptr;  // the current epoch's order and its inverse
+    int perm_epoch = -1;                   // epoch whose order perm holds
+    PartitionScratch pw{};
+    int64_t *d_mb_p0 = nullptr;            // M + 1 (random partition)
     float *master = nullptr;
     int levels = 0;                        // combine-tree levels in use
     float *slots = nullptr;                // all levels, in order
@@ -229,10 +246,14 @@ void release(f2v_ctx *c)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    void *bufs[] = {c->err_word, c->row_ptr, c->col_idx, c->item_u0, c->counter, c->apair,
-                    c->z[0], c->master};
+    void *bufs[] = {c->err_word, c->row_ptr0, c->col_idx0, c->item_u0, c->counter, c->apair0,
+                    c->z[0], c->master, c->perm, c->rank, c->pw.keys, c->pw.keys2, c->pw.vals,
+                    c->pw.deg, c->pw.cnt, c->pw.nch, c->pw.temp, c->d_mb_p0};
     for (void *p : bufs)
         if (p) cudaFree(p);
+    if (c->row_ptr != c->row_ptr0 && c->row_ptr) cudaFree(c->row_ptr);
+    if (c->col_idx != c->col_idx0 && c->col_idx) cudaFree(c->col_idx);
+    if (c->apair != c->apair0 && c->apair) cudaFree(c->apair);
     if (c->xstream) cudaStreamSynchronize(c->xstream);
     void *bulk_bufs[] = {c->d_mb_item_base, c->d_mb_C, c->row_flag, c->mb_done,
                          c->partner_buf[0], c->partner_buf[1]};
@@ -339,6 +360,21 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
         c->mb_item_base[(size_t)k + 1] = c->mb_item_base[(size_t)k] + nit;
         c->max_items = std::max(c->max_items, nit);
     }
+    c->mb_p0.assign((size_t)M + 1, 0);
+    for (int k = 0; k <= M; ++k)
+        c->mb_p0[(size_t)k] = c->h_apair[(size_t)std::min<int64_t>(n, (int64_t)k * c->b)];
+    if (c->partition) {
+        // any b vertices may share a minibatch: size for the b largest
+        std::vector<int64_t> cnt((size_t)n);
+        for (int u = 0; u < n; ++u) cnt[(size_t)u] = c->h_apair[(size_t)u + 1] - c->h_apair[(size_t)u];
+        const size_t top = std::min<size_t>((size_t)c->b, cnt.size());
+        std::partial_sort(cnt.begin(), cnt.begin() + top, cnt.end(), std::greater<int64_t>());
+        int64_t maxPk = 0;
+        for (size_t i = 0; i < top; ++i) maxPk += cnt[i];
+        if (maxPk >= (int64_t)INT32_MAX - 32) return false;
+        const int64_t worst = c->bulk ? std::max<int64_t>(W, 1) : (maxPk + c->C - 1) / c->C;
+        c->max_items = std::max(c->max_items, worst);
+    }
     return true;
 }
 
@@ -408,20 +444,36 @@ int num_minibatches(const f2v_ctx *c) { return (c->n + c->b - 1) / c->b; }
 // The staged kernel reads every pair's partner from an expanded list, and
 // so does the register kernel in the rForce2Vec form (walks are drawn once
 // per epoch into the list).
-bool uses_partner_list(const f2v_ctx *c) { return c->bulk || c->walk > 0 || c->shared; }
+bool uses_partner_list(const f2v_ctx *c)
+{
+    return c->bulk || c->walk > 0 || c->shared || c->partition;
+}
 
-cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st)
+// The partner list of `epoch` for the graph the kernels walk (given = true:
+// for the graph as given, in id order).
+cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st,
+                                bool given = false)
 {
     c->launches++;
     const int32_t shared_b = c->shared ? c->b : 0;
+    const bool relabelled = c->partition && !given;
+    const int32_t *rp = given ? c->row_ptr0 : c->row_ptr;
+    const int32_t *ci = given ? c->col_idx0 : c->col_idx;
+    const int64_t *ap = given ? c->apair0 : c->apair;
+    const int32_t *perm = relabelled ? c->perm : nullptr;
+    const int32_t *rank = relabelled ? c->rank : nullptr;
     if (c->walk > 0)
-        return launch_expand_walks(c->row_ptr, c->col_idx, c->apair, c->n, c->s, c->walk,
-                                   shared_b, (uint32_t)epoch, (uint32_t)c->seed,
-                                   (uint32_t)(c->seed >> 32), buf, st);
-    return launch_expand_partners(c->row_ptr, c->col_idx, c->apair, c->n, c->s, shared_b,
-                                  (uint32_t)epoch, (uint32_t)c->seed, (uint32_t)(c->seed >> 32),
-                                  buf, st);
+        return launch_expand_walks(rp, ci, ap, c->n, c->s, c->walk, shared_b, perm, rank,
+                                   (uint32_t)epoch, (uint32_t)c->seed, (uint32_t)(c->seed >> 32),
+                                   buf, st);
+    return launch_expand_partners(rp, ci, ap, c->n, c->s, shared_b, perm, rank, (uint32_t)epoch,
+                                  (uint32_t)c->seed, (uint32_t)(c->seed >> 32), buf, st);
 }
+
+// Buffers (and their row offsets in the TMA map) the epoch reads from and
+// writes to.
+int zcur_index(const f2v_ctx *c) { return c->partition ? (c->cur ^ 1) : c->cur; }
+int znext_index(const f2v_ctx *c) { return c->partition ? 2 : (c->cur ^ 1); }
 
 // Reads (and clears) the device error word after the stream has drained.
 // A set word means a bounded device wait ran out: the epoch's result is not
@@ -449,14 +501,15 @@ void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
     a.col_idx = c->col_idx;
     a.apair = c->apair;
     a.item_u0 = c->item_u0 + c->mb_item_base[(size_t)k];
-    a.zcur = (const Ts *)c->z[c->cur];
-    a.znext = (Ts *)c->z[c->cur ^ 1];
+    a.zcur = (const Ts *)c->z[zcur_index(c)];
+    a.znext = (Ts *)c->z[znext_index(c)];
     a.counter = c->counter;
     a.slots = c->slots;
     a.unit_cnt = c->unit_cnt;
     a.units0 = std::max<int64_t>(c->max_items, 1);
-    a.P0 = c->h_apair[(size_t)u0];
-    a.Pk = (int32_t)(c->h_apair[(size_t)u1] - a.P0);
+    (void)u1;
+    a.P0 = c->mb_p0[(size_t)k];
+    a.Pk = (int32_t)(c->mb_p0[(size_t)k + 1] - a.P0);
     a.n_items = (int32_t)(c->mb_item_base[(size_t)k + 1] - c->mb_item_base[(size_t)k]);
     a.mb_begin = u0;
     a.mb_end = u1;
@@ -468,7 +521,8 @@ void fill_args(const f2v_ctx *c, int k, float eta, ForceArgs<Ts> &a)
     a.eta = eta;
     a.model = c->model;
     a.err = c->err_word;
-    a.partner = (c->walk > 0 || c->shared) ? c->partner_buf[c->epoch & 1] : nullptr;
+    a.partner = (c->walk > 0 || c->shared || c->partition) ? c->partner_buf[c->epoch & 1]
+                                                            : nullptr;
 }
 
 template <typename Ts>
@@ -490,21 +544,63 @@ void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochA
     ea.k_end = k_end;
     ea.b = c->b;
     ea.ring = c->ring;
-    ea.zcur_row0 = c->cur * c->n;
-    ea.znext_row0 = (c->cur ^ 1) * c->n;
-    ea.own_row0 = (c->precision == F2V_BF16) ? 0 : c->cur * c->n;
+    ea.zcur_row0 = zcur_index(c) * c->n;
+    ea.znext_row0 = znext_index(c) * c->n;
+    ea.own_row0 = (c->precision == F2V_BF16) ? 0 : zcur_index(c) * c->n;
 }
 
 // Launches the force kernel(s) for minibatches [k_begin, k_end) of the
 // current epoch: one persistent launch for the staged kernel, one launch
 // per minibatch for the register kernel.  Each launch is bracketed by timing
 // events when timing is on.
+// Random partition: at the start of epoch e, the order of e (once per
+// epoch), the graph relabelled into it with its pair prefix and chunk tables,
+// and Z gathered into it (every time the epoch starts, since Z may have been
+// set or synchronised since).
+f2v_status prepare_partition(f2v_ctx *c, int e)
+{
+    const int M = num_minibatches(c);
+    if (c->perm_epoch != e) {
+        F2V_CUDA(c, launch_partition(c->n, (uint32_t)e, (uint32_t)c->seed,
+                                     (uint32_t)(c->seed >> 32), c->pw, c->perm, c->rank,
+                                     c->stream));
+        F2V_CUDA(c, launch_relabel(c->row_ptr0, c->col_idx0, c->perm, c->rank, c->n, c->s,
+                                   c->walk, c->pw, c->row_ptr, c->col_idx, c->apair, c->stream));
+        const int64_t W = c->bulk ? (int64_t)c->bulk_sms * c->bulk_warps : 0;
+        F2V_CUDA(c, launch_mb_tables(c->apair, c->n, c->b, M, W, c->C, c->pw, c->d_mb_C,
+                                     c->d_mb_item_base, c->item_u0, c->d_mb_p0, c->stream));
+        c->launches += 9;
+        if (!c->bulk) {
+            // the register kernel takes each minibatch's tables from the host
+            F2V_CUDA(c, cudaMemcpyAsync(c->mb_C.data(), c->d_mb_C, sizeof(int32_t) * M,
+                                        cudaMemcpyDeviceToHost, c->stream));
+            F2V_CUDA(c, cudaMemcpyAsync(c->mb_item_base.data(), c->d_mb_item_base,
+                                        sizeof(int64_t) * (M + 1), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            F2V_CUDA(c, cudaMemcpyAsync(c->mb_p0.data(), c->d_mb_p0, sizeof(int64_t) * (M + 1),
+                                        cudaMemcpyDeviceToHost, c->stream));
+            F2V_CUDA(c, cudaStreamSynchronize(c->stream));
+        }
+        // partner lists belong to one order
+        c->partner_epoch[0] = c->partner_epoch[1] = -1;
+        c->perm_epoch = e;
+    }
+    F2V_CUDA(c, launch_permute_rows((const float *)c->z[c->cur], (float *)c->z[c->cur ^ 1],
+                                    c->perm, c->n, c->ld, false, c->stream));
+    c->launches++;
+    return F2V_OK;
+}
+
 f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
 {
     const int e = c->epoch;
     const float eta = (float)lr_for_epoch(c, e);
     const int step = c->bulk ? (k_end - k_begin) : 1;
     const int slot = e & 1;
+    if (c->partition && k_begin == 0) {
+        f2v_status pst = prepare_partition(c, e);
+        if (pst != F2V_OK) return pst;
+    }
     const bool listed = uses_partner_list(c);
     if (listed && c->partner_epoch[slot] != e) {   // this epoch's partner list, now
         // (after any list still being written ahead into this buffer)
@@ -519,7 +615,8 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     }
     // the other buffer's last reader (epoch e - 1) is done once the work
     // enqueued so far is: the next epoch's list may overwrite it from here
-    const bool prefetch = listed && k_end == num_minibatches(c) &&
+    // (not with a random partition: the next epoch's list needs its order)
+    const bool prefetch = listed && !c->partition && k_end == num_minibatches(c) &&
                           c->partner_epoch[slot ^ 1] != e + 1;
     if (prefetch) F2V_CUDA(c, cudaEventRecord(c->ev_xfree[slot ^ 1], c->stream));
     if (c->bulk)
@@ -585,6 +682,12 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
         F2V_CUDA(c, cudaEventRecord(c->ev_xdone[ns], c->xstream));
         c->partner_epoch[ns] = e + 1;
     }
+    if (c->partition && k_end == num_minibatches(c)) {
+        // the epoch's rows back into id order
+        F2V_CUDA(c, launch_permute_rows((const float *)c->z[2], (float *)c->z[c->cur], c->perm,
+                                        c->n, c->ld, true, c->stream));
+        c->launches++;
+    }
     return F2V_OK;
 }
 
@@ -595,7 +698,7 @@ void advance(f2v_ctx *c, int count)
     c->mb_pos += count;
     if (c->mb_pos == num_minibatches(c)) {
         c->mb_pos = 0;
-        c->cur ^= 1;
+        if (!c->partition) c->cur ^= 1;   // (a partition scatters into z[cur])
         c->epoch++;
     }
 }
@@ -618,6 +721,12 @@ f2v_status sync_current(f2v_ctx *c)
 {
     if (c->mb_pos == 0) return F2V_OK;
     const size_t rows = std::min<size_t>((size_t)c->mb_pos * c->b, (size_t)c->n);
+    if (c->partition) {   // the updated positions, back to their ids
+        F2V_CUDA(c, launch_permute_rows((const float *)c->z[2], (float *)c->z[c->cur], c->perm,
+                                        (int64_t)rows, c->ld, true, c->stream));
+        c->launches++;
+        return F2V_OK;
+    }
     const size_t bytes = rows * (size_t)c->ld * elem_size(c);
     F2V_CUDA(c, cudaMemcpyAsync(c->z[c->cur], c->z[c->cur ^ 1], bytes, cudaMemcpyDeviceToDevice,
                                 c->stream));
@@ -683,6 +792,11 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
     c->n = n; c->d = d; c->ld = d; c->s = s; c->b = minibatch; c->model = (int)model;
     c->walk = walk;
     c->shared = (flags & F2V_FLAG_SHARED_SAMPLES) != 0;
+    c->partition = (flags & F2V_FLAG_RANDOM_PARTITION) != 0;
+    if (c->partition && precision != F2V_FP32) {
+        delete c;
+        return fail(nullptr, F2V_EINVAL, "F2V_FLAG_RANDOM_PARTITION needs F2V_FP32 storage");
+    }
     c->precision = precision; c->seed = seed; c->lr = lr;
     c->stream = (cudaStream_t)stream;
     c->nnz = row_ptr[n];
@@ -720,14 +834,41 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
     const size_t zbytes = (size_t)n * (size_t)c->ld * es;
     st = F2V_OK;
     if (st == F2V_OK) st = alloc(c, (void **)&c->err_word, sizeof(int32_t));
-    if (st == F2V_OK) st = alloc(c, (void **)&c->row_ptr, sizeof(int32_t) * ((size_t)n + 1));
-    if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx, sizeof(int32_t) * (size_t)c->nnz);
-    if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
+    if (st == F2V_OK) st = alloc(c, (void **)&c->row_ptr0, sizeof(int32_t) * ((size_t)n + 1));
+    if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx0, sizeof(int32_t) * (size_t)c->nnz);
+    if (st == F2V_OK) st = alloc(c, (void **)&c->apair0, sizeof(int64_t) * ((size_t)n + 1));
+    if (st == F2V_OK) {
+        c->row_ptr = c->row_ptr0;
+        c->col_idx = c->col_idx0;
+        c->apair = c->apair0;
+    }
+    if (st == F2V_OK && c->partition) {
+        // the relabelled graph, the epoch's order and the scratch that builds them
+        const size_t M = c->mb_C.size();
+        st = alloc(c, (void **)&c->row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx, sizeof(int32_t) * (size_t)c->nnz);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->perm, sizeof(int32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->rank, sizeof(int32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.keys, sizeof(uint32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.keys2, sizeof(uint32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.vals, sizeof(int32_t) * (size_t)n);
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.deg, sizeof(int32_t) * ((size_t)n + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.cnt, sizeof(int64_t) * ((size_t)n + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->pw.nch, sizeof(int64_t) * (M + 1));
+        if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_p0, sizeof(int64_t) * (M + 1));
+        c->pw.temp_bytes = std::max<size_t>(partition_temp_bytes(n, (int32_t)M), 16);
+        if (st == F2V_OK) st = alloc(c, &c->pw.temp, c->pw.temp_bytes);
+        // chunk tables of any order: at most one chunk per 32 pairs plus one per minibatch
+        const size_t worst = (size_t)(c->h_apair[(size_t)n] / 32) + M + 1;
+        if (items.size() < worst) items.resize(worst, 0);
+    }
     if (st == F2V_OK) st = alloc(c, (void **)&c->item_u0, sizeof(int32_t) * items.size());
     if (st == F2V_OK) st = alloc(c, (void **)&c->counter, sizeof(int32_t) * (size_t)n);
-    // both Z buffers in one allocation: one TMA map then covers either
-    if (st == F2V_OK) st = alloc(c, &c->z[0], 2 * zbytes);
-    if (st == F2V_OK) c->z[1] = static_cast<char *>(c->z[0]) + zbytes;
+    // Z buffers in one allocation: one TMA map then covers all of them
+    const int nz = c->partition ? 3 : 2;
+    if (st == F2V_OK) st = alloc(c, &c->z[0], nz * zbytes);
+    for (int i = 1; i < nz && st == F2V_OK; ++i) c->z[i] = static_cast<char *>(c->z[0]) + i * zbytes;
     if (st == F2V_OK && precision == F2V_BF16)
         st = alloc(c, (void **)&c->master, (size_t)n * c->ld * sizeof(float));
     // combine tree: level l has ceil(max_items / 16^l) units, two slots each
@@ -755,15 +896,18 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
                             c->stream) != cudaSuccess)
             st = fail(c, F2V_ECUDA, "memset of combine counters failed");
     }
-    if (st == F2V_OK && c->bulk) {
+    if (st == F2V_OK && (c->bulk || c->partition)) {
         const size_t M = c->mb_C.size();
         st = alloc(c, (void **)&c->d_mb_item_base, sizeof(int64_t) * (M + 1));
         if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
+    }
+    if (st == F2V_OK && c->bulk) {
+        const size_t M = c->mb_C.size();
         if (st == F2V_OK) st = alloc(c, (void **)&c->row_flag, sizeof(int32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->mb_done, sizeof(int32_t) * 2 * M);
         std::string merr;
         if (st == F2V_OK &&
-            (!make_row_map(&c->zmap, c->z[0], 2 * (int64_t)n, d, precision == F2V_BF16, &merr) ||
+            (!make_row_map(&c->zmap, c->z[0], nz * (int64_t)n, d, precision == F2V_BF16, &merr) ||
              (precision == F2V_BF16 &&
               !make_row_map(&c->mmap, c->master, (int64_t)n, d, false, &merr))))
             st = fail(c, F2V_ECUDA, "tensor map: %s", merr.c_str());
@@ -796,24 +940,27 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
             return F2V_ECUDA;                                                        \
         }                                                                            \
     } while (0)
-    CREATE_CUDA(cudaMemcpyAsync(c->row_ptr, row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+    CREATE_CUDA(cudaMemcpyAsync(c->row_ptr0, row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                                 cudaMemcpyHostToDevice, c->stream));
     if (c->nnz)
-        CREATE_CUDA(cudaMemcpyAsync(c->col_idx, col_idx, sizeof(int32_t) * (size_t)c->nnz,
+        CREATE_CUDA(cudaMemcpyAsync(c->col_idx0, col_idx, sizeof(int32_t) * (size_t)c->nnz,
                                     cudaMemcpyHostToDevice, c->stream));
-    CREATE_CUDA(cudaMemcpyAsync(c->apair, c->h_apair.data(), sizeof(int64_t) * ((size_t)n + 1),
+    CREATE_CUDA(cudaMemcpyAsync(c->apair0, c->h_apair.data(), sizeof(int64_t) * ((size_t)n + 1),
                                 cudaMemcpyHostToDevice, c->stream));
     if (!items.empty())
         CREATE_CUDA(cudaMemcpyAsync(c->item_u0, items.data(), sizeof(int32_t) * items.size(),
                                     cudaMemcpyHostToDevice, c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->counter, 0, sizeof(int32_t) * (size_t)n, c->stream));
     CREATE_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(int32_t), c->stream));
-    if (c->bulk) {
+    if (c->bulk || c->partition) {
         const size_t M = c->mb_C.size();
         CREATE_CUDA(cudaMemcpyAsync(c->d_mb_item_base, c->mb_item_base.data(),
                                     sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice, c->stream));
         CREATE_CUDA(cudaMemcpyAsync(c->d_mb_C, c->mb_C.data(), sizeof(int32_t) * M,
                                     cudaMemcpyHostToDevice, c->stream));
+    }
+    if (c->bulk) {
+        const size_t M = c->mb_C.size();
         CREATE_CUDA(cudaMemsetAsync(c->row_flag, 0, sizeof(int32_t) * (size_t)n, c->stream));
         CREATE_CUDA(cudaMemsetAsync(c->mb_done, 0, sizeof(int32_t) * 2 * M, c->stream));
     }
@@ -959,7 +1106,16 @@ f2v_status f2v_set_embedding(f2v_ctx *ctx, const float *z, size_t count)
         F2V_CUDA(ctx, cudaMemcpyAsync(ctx->z[ctx->cur], z, want * sizeof(float),
                                       cudaMemcpyHostToDevice, ctx->stream));
     }
-    if (ctx->mb_pos > 0) {   // mid-epoch: updated rows are read from the next buffer
+    if (ctx->mb_pos > 0 && ctx->partition) {
+        // mid-epoch: the epoch reads Z in its order, updated positions from z[2]
+        const size_t rows = std::min<size_t>((size_t)ctx->mb_pos * ctx->b, (size_t)ctx->n);
+        F2V_CUDA(ctx, launch_permute_rows((const float *)ctx->z[ctx->cur],
+                                          (float *)ctx->z[ctx->cur ^ 1], ctx->perm, ctx->n,
+                                          ctx->ld, false, ctx->stream));
+        F2V_CUDA(ctx, launch_permute_rows((const float *)ctx->z[ctx->cur], (float *)ctx->z[2],
+                                          ctx->perm, (int64_t)rows, ctx->ld, false, ctx->stream));
+        ctx->launches += 2;
+    } else if (ctx->mb_pos > 0) {   // mid-epoch: updated rows are read from the next buffer
         const size_t rows = std::min<size_t>((size_t)ctx->mb_pos * ctx->b, (size_t)ctx->n);
         F2V_CUDA(ctx, cudaMemcpyAsync(ctx->z[ctx->cur ^ 1], ctx->z[ctx->cur],
                                       rows * (size_t)ctx->ld * elem_size(ctx),
@@ -1060,11 +1216,26 @@ f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t c
     int32_t *dbuf = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&dbuf, want * sizeof(int32_t), ctx->stream);
     if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "debug_samples: %s", cudaGetErrorString(e));
+    // shared samples under a random partition: a vertex's minibatch is its
+    // position in that epoch's order
+    int32_t *tperm = nullptr, *trank = nullptr;
+    if (ctx->partition && ctx->shared) {
+        e = cudaMallocAsync((void **)&tperm, sizeof(int32_t) * (size_t)ctx->n, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMallocAsync((void **)&trank, sizeof(int32_t) * (size_t)ctx->n, ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "debug_samples: %s", cudaGetErrorString(e));
+        F2V_CUDA(ctx, launch_partition(ctx->n, (uint32_t)epoch, (uint32_t)ctx->seed,
+                                       (uint32_t)(ctx->seed >> 32), ctx->pw, tperm, trank,
+                                       ctx->stream));
+        ctx->launches += 3;
+    }
     const int blocks = (int)std::min<int64_t>(((int64_t)want + 255) / 256, 152 * 16);
     samples_kernel<<<blocks, 256, 0, ctx->stream>>>(dbuf, ctx->n, ctx->s,
-                                                     ctx->shared ? ctx->b : 0, (uint32_t)epoch,
-                                                     (uint32_t)ctx->seed,
+                                                     ctx->shared ? ctx->b : 0, trank,
+                                                     (uint32_t)epoch, (uint32_t)ctx->seed,
                                                      (uint32_t)(ctx->seed >> 32));
+    if (tperm) F2V_CUDA(ctx, cudaFreeAsync(tperm, ctx->stream));
+    if (trank) F2V_CUDA(ctx, cudaFreeAsync(trank, ctx->stream));
     ctx->launches++;
     F2V_CUDA(ctx, cudaGetLastError());
     F2V_CUDA(ctx, cudaMemcpyAsync(out, dbuf, want * sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -1093,8 +1264,8 @@ f2v_status f2v_debug_walks(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t cou
         return fail(ctx, F2V_ENOMEM, "debug_walks: %s", cudaGetErrorString(e));
     }
     // the list the epoch's force launches read, written by the same kernel
-    F2V_CUDA(ctx, launch_partner_list(ctx, epoch, list, ctx->stream));
-    F2V_CUDA(ctx, launch_extract_walks(ctx->apair, ctx->row_ptr, ctx->n, ctx->walk, list, dout,
+    F2V_CUDA(ctx, launch_partner_list(ctx, epoch, list, ctx->stream, true));
+    F2V_CUDA(ctx, launch_extract_walks(ctx->apair0, ctx->row_ptr0, ctx->n, ctx->walk, list, dout,
                                        ctx->stream));
     ctx->launches++;
     F2V_CUDA(ctx, cudaMemcpyAsync(out, dout, want * sizeof(int32_t), cudaMemcpyDeviceToHost,

@@ -35,16 +35,15 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
 // of 2^-24 in [-0.5, 0.5), exact in FP32 (the initial embedding, uniform as
 // the paper's random start).
 // Negative sample k of vertex u in epoch `epoch`: its own draw
-// Philox(ctr = (u, epoch, k, 0)).x0 mod n, or, with shared_b > 0 (one set S_b
-// per minibatch, the literal Alg. 1 line 6), the draw of u's minibatch
-// Philox(ctr = (u / shared_b, epoch, k, 2)).x0 mod n.
-__device__ __forceinline__ uint32_t negative_sample(int64_t u, uint32_t epoch, uint32_t k,
-                                                    int32_t shared_b, int32_t n, uint32_t key0,
+// Philox(ctr = (u, epoch, k, 0)).x0 mod n, or, with kb >= 0 (one set S_b
+// per minibatch, the literal Alg. 1 line 6), the draw of minibatch kb,
+// Philox(ctr = (kb, epoch, k, 2)).x0 mod n.
+__device__ __forceinline__ uint32_t negative_sample(int64_t u, int64_t kb, uint32_t epoch,
+                                                    uint32_t k, int32_t n, uint32_t key0,
                                                     uint32_t key1)
 {
-    const uint32_t x = (shared_b > 0)
-                           ? philox_x0((uint32_t)(u / shared_b), epoch, k, 2u, key0, key1)
-                           : philox_x0((uint32_t)u, epoch, k, 0u, key0, key1);
+    const uint32_t x = (kb >= 0) ? philox_x0((uint32_t)kb, epoch, k, 2u, key0, key1)
+                                 : philox_x0((uint32_t)u, epoch, k, 0u, key0, key1);
     return x % (uint32_t)n;
 }
 

@@ -28,8 +28,10 @@ namespace {
 __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
                                        const int32_t *__restrict__ col_idx,
                                        const int64_t *__restrict__ apair, int32_t n, int32_t s,
-                                       int32_t shared_b, uint32_t epoch, uint32_t key0,
-                                       uint32_t key1, int32_t *__restrict__ partner)
+                                       int32_t shared_b, const int32_t *__restrict__ perm,
+                                       const int32_t *__restrict__ rank, uint32_t epoch,
+                                       uint32_t key0, uint32_t key1,
+                                       int32_t *__restrict__ partner)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -39,9 +41,12 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
         const int32_t r0 = row_ptr[u];
         const int32_t deg = row_ptr[u + 1] - r0;
         for (int32_t j = lane; j < deg; j += 32) partner[base + j] = col_idx[r0 + j];
+        const int64_t uo = perm ? perm[u] : u;                // the original id
+        const int64_t kb = shared_b > 0 ? u / shared_b : -1;   // u's minibatch
         for (int32_t k = lane; k < s; k += 32) {
-            const uint32_t w = negative_sample(u, epoch, (uint32_t)k, shared_b, n, key0, key1);
-            partner[base + deg + k] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
+            const uint32_t w = negative_sample(uo, kb, epoch, (uint32_t)k, n, key0, key1);
+            partner[base + deg + k] =
+                ((int64_t)w == uo) ? kPartnerNone : -2 - (rank ? rank[w] : (int32_t)w);
         }
         if (deg + s == 0 && lane == 0) partner[base] = kPartnerNone;   // the empty pair
     }
@@ -53,12 +58,15 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
 __global__ void expand_walks_kernel(const int32_t *__restrict__ row_ptr,
                                     const int32_t *__restrict__ col_idx,
                                     const int64_t *__restrict__ apair, int32_t n, int32_t s,
-                                    int32_t walk, int32_t shared_b, uint32_t epoch, uint32_t key0,
-                                    uint32_t key1, int32_t *__restrict__ partner)
+                                    int32_t walk, int32_t shared_b,
+                                    const int32_t *__restrict__ perm,
+                                    const int32_t *__restrict__ rank, uint32_t epoch,
+                                    uint32_t key0, uint32_t key1, int32_t *__restrict__ partner)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += stride) {
         int64_t p = apair[u];
+        const int64_t uo = perm ? perm[u] : u;                // the original id
         const bool has_walk = row_ptr[u + 1] > row_ptr[u];
         if (has_walk) {
             int32_t w = (int32_t)u;
@@ -71,7 +79,7 @@ __global__ void expand_walks_kernel(const int32_t *__restrict__ row_ptr,
                     if (deg == 0) {
                         stopped = true;
                     } else {
-                        const uint32_t x = philox_x0((uint32_t)u, epoch, (uint32_t)i, 1u, key0,
+                        const uint32_t x = philox_x0((uint32_t)uo, epoch, (uint32_t)i, 1u, key0,
                                                      key1);
                         w = col_idx[lo + (int32_t)(x % (uint32_t)deg)];
                         code = ((int64_t)w == u) ? kPartnerNone : w;
@@ -80,9 +88,10 @@ __global__ void expand_walks_kernel(const int32_t *__restrict__ row_ptr,
                 partner[p++] = code;
             }
         }
+        const int64_t kb = shared_b > 0 ? u / shared_b : -1;   // u's minibatch
         for (int32_t k = 0; k < s; ++k) {
-            const uint32_t w = negative_sample(u, epoch, (uint32_t)k, shared_b, n, key0, key1);
-            partner[p++] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
+            const uint32_t w = negative_sample(uo, kb, epoch, (uint32_t)k, n, key0, key1);
+            partner[p++] = ((int64_t)w == uo) ? kPartnerNone : -2 - (rank ? rank[w] : (int32_t)w);
         }
         if (!has_walk && s == 0) partner[p] = kPartnerNone;   // the empty pair
     }
@@ -113,11 +122,13 @@ int grid_for(int64_t threads)
 
 cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
                                 const int64_t *apair, int32_t n, int32_t s, int32_t walk,
-                                int32_t shared_b, uint32_t epoch, uint32_t key0, uint32_t key1,
-                                int32_t *partner, cudaStream_t st)
+                                int32_t shared_b, const int32_t *perm, const int32_t *rank,
+                                uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
+                                cudaStream_t st)
 {
     expand_walks_kernel<<<grid_for(n), 256, 0, st>>>(row_ptr, col_idx, apair, n, s, walk,
-                                                     shared_b, epoch, key0, key1, partner);
+                                                     shared_b, perm, rank, epoch, key0, key1,
+                                                     partner);
     return cudaGetLastError();
 }
 
@@ -132,7 +143,8 @@ cudaError_t launch_extract_walks(const int64_t *apair, const int32_t *row_ptr, i
 
 cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
                                    const int64_t *apair, int32_t n, int32_t s, int32_t shared_b,
-                                   uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
+                                   const int32_t *perm, const int32_t *rank, uint32_t epoch,
+                                   uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st)
 {
     int dev = 0, sms = 0;
@@ -141,8 +153,8 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
     const int64_t warps_needed = n;
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)std::max(sms, 1) * 16));
-    expand_partners_kernel<<<blocks, 256, 0, st>>>(row_ptr, col_idx, apair, n, s, shared_b,
-                                                   epoch, key0, key1, partner);
+    expand_partners_kernel<<<blocks, 256, 0, st>>>(row_ptr, col_idx, apair, n, s, shared_b, perm,
+                                                   rank, epoch, key0, key1, partner);
     return cudaGetLastError();
 }
 

@@ -109,9 +109,12 @@ constexpr int32_t kPartnerNone = -1;
 // Writes the partner code of every pair of epoch `epoch` (pair apair[u] + j
 // of vertex u), one warp per vertex.  shared_b > 0: the samples are the
 // shared set of u's minibatch of that size (negative_sample).
+// perm, rank (may be null): the graph is relabelled by a random partition;
+// samples keep the counters of the original ids and are mapped to ranks.
 cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_idx,
                                    const int64_t *apair, int32_t n, int32_t s, int32_t shared_b,
-                                   uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
+                                   const int32_t *perm, const int32_t *rank, uint32_t epoch,
+                                   uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st);
 
 // rForce2Vec (Algorithm 3): the same list with vertex u's first `walk` pairs
@@ -120,8 +123,40 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
 // Philox(key, ctr = (u, epoch, i, 1)).x0 mod deg(w).
 cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
                                 const int64_t *apair, int32_t n, int32_t s, int32_t walk,
-                                int32_t shared_b, uint32_t epoch, uint32_t key0, uint32_t key1,
-                                int32_t *partner, cudaStream_t st);
+                                int32_t shared_b, const int32_t *perm, const int32_t *rank,
+                                uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
+                                cudaStream_t st);
+
+// The random partition of an epoch (Algorithm 1 line 3), f2v_partition.cu.
+struct PartitionScratch {
+    uint32_t *keys, *keys2;    // n: sort keys
+    int32_t *vals;             // n: sort values (vertex ids)
+    int32_t *deg;              // n + 1
+    int64_t *cnt;              // n + 1
+    int64_t *nch;              // M + 1
+    void *temp;                // CUB temporary storage
+    size_t temp_bytes;
+};
+size_t partition_temp_bytes(int32_t n, int32_t M);
+// perm[p]: the vertex at position p in epoch `epoch`'s order (Philox key
+// ctr = (v, epoch, 0, 3), ties by id); rank = its inverse.
+cudaError_t launch_partition(int32_t n, uint32_t epoch, uint32_t key0, uint32_t key1,
+                             const PartitionScratch &w, int32_t *perm, int32_t *rank,
+                             cudaStream_t st);
+// The graph relabelled into that order (row p = neighbours of perm[p] as
+// ranks, in CSR order) and its pair prefix.
+cudaError_t launch_relabel(const int32_t *row_ptr, const int32_t *col_idx, const int32_t *perm,
+                           const int32_t *rank, int32_t n, int32_t s, int32_t walk,
+                           const PartitionScratch &w, int32_t *row_ptr2, int32_t *col_idx2,
+                           int64_t *apair2, cudaStream_t st);
+// Chunk sizes (staged kernel: W warps; register kernel: W = 0, Cfix pairs),
+// chunk offsets, chunk start vertices and minibatch pair offsets (M + 1).
+cudaError_t launch_mb_tables(const int64_t *apair2, int32_t n, int32_t b, int32_t M, int64_t W,
+                             int32_t Cfix, const PartitionScratch &w, int32_t *mb_C,
+                             int64_t *mb_base, int32_t *items, int64_t *mb_p0, cudaStream_t st);
+// dst[p] = src[perm[p]] (gather) or dst[perm[p]] = src[p] (scatter), FP32 rows.
+cudaError_t launch_permute_rows(const float *src, float *dst, const int32_t *perm, int64_t rows,
+                                int32_t d, bool scatter, cudaStream_t st);
 
 // out[u * walk + i]: the code of walk step i of vertex u in the list
 // `partner` (kPartnerNone for a vertex without neighbours).

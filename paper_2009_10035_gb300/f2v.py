@@ -25,6 +25,7 @@ LR_LINEAR = 1
 FLAG_CHECK_SYMMETRY = 0x1
 FLAG_NO_STAGING = 0x2
 FLAG_SHARED_SAMPLES = 0x4
+FLAG_RANDOM_PARTITION = 0x8
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(6)
 _STATUS = {0: "F2V_OK", 1: "F2V_EINVAL", 2: "F2V_ENOMEM", 3: "F2V_ECUDA",

@@ -614,3 +614,118 @@ def test_rmat_scale20_d128_shared_samples(model, rmat20):
     worst = check_steps(g, 128, model, 5, b, lr=0.02, seed=1, steps=steps,
                         flags=f2v.FLAG_SHARED_SAMPLES, schedule=f2v.LR_LINEAR, total_epochs=20)
     print(f"rmat20 shared samples model={model}: worst scaled error {worst:.3e}")
+
+
+# ---------------------------------------------------------------- random partition (Alg. 1 line 3)
+
+def check_partition_steps(g, d, model, s, b, lr=0.05, seed=4, epochs=2, steps=None, flags=0,
+                          walk=0, tol=TOL_STEP):
+    """As check_steps, with a new random partition every epoch: minibatch k
+    of epoch e is the vertex list oracle.partition(n, e)[k b : (k+1) b]."""
+    M = -(-g.n // b)
+    shared = bool(flags & f2v.FLAG_SHARED_SAMPLES)
+    worst = 0.0
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                     seed=seed, flags=flags | f2v.FLAG_RANDOM_PARTITION,
+                     walk_length=walk) as ctx:
+        for e in range(epochs):
+            perm = oracle.partition(g.n, e, seed)
+            for k in range(M):
+                if steps is not None and (e, k) not in steps:
+                    ctx.run_minibatches(1)
+                    continue
+                before = ctx.embedding().astype(np.float64)
+                ctx.run_minibatches(1)
+                after = ctx.embedding().astype(np.float64)
+                verts = perm[k * b:min(g.n, (k + 1) * b)]
+                G, A = oracle.grad_vertices_abs(model, g.row_ptr, g.col_idx, before, verts, s,
+                                                seed, e, walk=walk,
+                                                shared_k=k if shared else -1)
+                want = before[verts] - lr * G
+                if model != f2v.TDIST:
+                    want = np.clip(want, -4.0, 4.0)
+                scale = np.maximum(np.abs(before[verts]) + lr * A, FLOOR)
+                err = np.abs(after[verts] - want) / scale
+                assert np.isfinite(after).all()
+                assert err.max() <= tol, f"epoch {e} minibatch {k}: scaled err {err.max():.3e}"
+                rest = np.ones(g.n, bool)
+                rest[verts] = False
+                assert np.array_equal(after[rest], before[rest])
+                worst = max(worst, float(err.max()))
+    return worst
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("d", [8, 32, 128])
+def test_partition_steps(model, d):
+    """Register kernel (d = 8, 32) and staged kernel (d = 128) on the graph
+    relabelled into each epoch's order."""
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_partition_steps(g, d, model, 4, 256, steps={(0, 0), (0, 3), (1, 2), (1, 5)})
+
+
+@pytest.mark.parametrize("d", [32, 128])
+def test_partition_with_walks_shared_samples_and_fr(d):
+    g = graphs.erdos_renyi(1500, p=0.004, seed=8)
+    check_partition_steps(g, d, f2v.SIGMOID, 4, 256, epochs=1, steps={(0, 1), (0, 4)}, walk=5)
+    check_partition_steps(g, d, f2v.TDIST, 4, 256, epochs=2, steps={(0, 2), (1, 4)},
+                          flags=f2v.FLAG_SHARED_SAMPLES)
+    check_partition_steps(g, d, f2v.FR, 4, 256, lr=0.01, epochs=1, steps={(0, 3)})
+
+
+@pytest.mark.parametrize("d", [32, 128])
+def test_partition_whole_epochs(d):
+    g = graphs.config1_graph()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, s=5, lr=0.02, minibatch=256, seed=1,
+                     flags=f2v.FLAG_RANDOM_PARTITION) as ctx:
+        ctx.train(3)
+        got = ctx.embedding()
+    Z0 = oracle.init_embedding(g.n, d, 1)
+    want = oracle.train(f2v.TDIST, g.row_ptr, g.col_idx, Z0, 5, 256, 1, 0.02, 3, partition=True)
+    err = rel_err(got, want)
+    assert err.max() <= 3 * TOL_1EPOCH, float(err.max())
+
+
+def test_partition_samples_and_interruptions():
+    g = graphs.erdos_renyi(1200, p=0.005, seed=11)
+    flags = f2v.FLAG_RANDOM_PARTITION | f2v.FLAG_SHARED_SAMPLES
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, s=5, minibatch=200, seed=3,
+                     flags=flags) as ctx:
+        for e in (0, 2):
+            perm = oracle.partition(g.n, e, 3)
+            rank = np.empty_like(perm)
+            rank[perm] = np.arange(g.n)
+            S = oracle.samples_shared(g.n * 1, 5, 200, e, 3)   # set of minibatch k in row k*200
+            want = np.stack([S[(rank[u] // 200) * 200] for u in range(g.n)])
+            np.testing.assert_array_equal(ctx.debug_samples(e), want)
+    # a run stopped mid-epoch, read, written back and resumed equals one that
+    # was not; and two runs agree bit for bit
+    outs = []
+    for stop in (None, 2):
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, 128, s=5, minibatch=200, seed=3,
+                         flags=f2v.FLAG_RANDOM_PARTITION) as ctx:
+            ctx.epoch()
+            if stop is not None:
+                ctx.run_minibatches(stop)
+                ctx.set_embedding(ctx.embedding())
+            ctx.epoch()
+            ctx.epoch()
+            outs.append(ctx.embedding())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_partition_needs_fp32():
+    g = graphs.erdos_renyi(100, p=0.05, seed=1)
+    with pytest.raises(f2v.F2VError):
+        f2v.Context(g.row_ptr, g.col_idx, g.n, 128, precision=f2v.BF16,
+                    flags=f2v.FLAG_RANDOM_PARTITION)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_rmat_scale20_d128_partition(model, rmat20):
+    g = rmat20
+    b = 4096
+    M = -(-g.n // b)
+    worst = check_partition_steps(g, 128, model, 5, b, lr=0.02, seed=1, epochs=1,
+                                  steps={(0, 0), (0, M // 2), (0, M - 1)})
+    print(f"rmat20 partition model={model}: worst scaled error {worst:.3e}")
