@@ -146,20 +146,20 @@ __global__ void part_p0_kernel(const int64_t *__restrict__ apair, int32_t n, int
         p0[k] = apair[min((int64_t)n, k * (int64_t)b)];
 }
 
-// dst[p] = src[perm[p]] (gather) or dst[perm[p]] = src[p] (scatter), rows p < rows.
+// dst[p] = src[perm[p]] (gather) or dst[perm[p]] = src[p] (scatter), rows
+// p < rows: one warp per row, consecutive lanes on consecutive elements.
 __global__ void permute_rows_kernel(const float *__restrict__ src, float *__restrict__ dst,
                                     const int32_t *__restrict__ perm, int64_t rows, int32_t d,
                                     bool scatter)
 {
-    const int64_t total = rows * d;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = t / d, j = t - p * d;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t p = warp; p < rows; p += nwarps) {
         const int64_t v = perm[p];
-        if (scatter)
-            dst[v * d + j] = src[t];
-        else
-            dst[t] = src[v * d + j];
+        const float *s = src + (scatter ? p : v) * d;
+        float *t = dst + (scatter ? v : p) * d;
+        for (int32_t j = lane; j < d; j += 32) t[j] = s[j];
     }
 }
 
@@ -233,7 +233,7 @@ cudaError_t launch_permute_rows(const float *src, float *dst, const int32_t *per
                                 int32_t d, bool scatter, cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
-    permute_rows_kernel<<<grid_of(rows * d), 256, 0, st>>>(src, dst, perm, rows, d, scatter);
+    permute_rows_kernel<<<grid_of(rows * 32), 256, 0, st>>>(src, dst, perm, rows, d, scatter);
     return cudaGetLastError();
 }
 
