@@ -24,6 +24,8 @@ Every function cites the passage it follows:
                   rForce2Vec, N(u) from Algorithm 3)
   loss_vertex     Eq. 2 with Eq. 3 (sigmoid) or Eq. 7 (t)
   scores, auc     held-out-edge link prediction, Mann-Whitney AUC
+  downstream      (submodule, numpy) Sec. IV's link prediction with Hadamard
+                  features and logistic regression, k-means and modularity
 """
 from __future__ import annotations
 
