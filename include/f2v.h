@@ -218,6 +218,38 @@ f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
    u < n, k < s (count must equal n*s).  For checking; synchronous. */
 f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count);
 
+/*
+ * Link prediction as in Sec. IV ("Link prediction"), on the current Z, in
+ * FP64 on the device.  Pair i of the combined list (pos_pairs[2*npos] with
+ * label 1, then neg_pairs[2*nneg] with label 0; host int32 (u, v)) has the
+ * Hadamard features x_i = z_u * z_v (element by element); train_mask[npos +
+ * nneg] (host, nonzero = training pair) splits the list.  An L2-regularised
+ * logistic regression, theta = (w, b) minimising sum_i log(1 + exp(-s_i
+ * (w . x_i + b))) + |w|^2 / 2 over the training pairs (s_i = +-1, the
+ * intercept unpenalised), is fitted by Newton's method until a step's
+ * max-norm is below 1e-10 or after 100 steps; *accuracy = (TP + TN) / (test
+ * pairs), a pair predicted positive when w . x + b > 0.  theta (d + 1
+ * doubles, w then b) is written if not NULL.  Needs d <= 150 and at least
+ * one training and one test pair.  Synchronous.
+ */
+f2v_status f2v_eval_link_lr(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
+                            const int32_t *neg_pairs, int64_t nneg, const uint8_t *train_mask,
+                            double *accuracy, double *theta);
+
+/*
+ * Clustering as in Sec. IV ("Clustering"), on the current Z, in FP64 on the
+ * device: Lloyd's k-means from the centres z_{init[c]} (host, k vertex ids,
+ * 1 <= k <= 64, d <= 256), a vertex joining its nearest centre (the lowest
+ * index on a tie), a centre moving to its cluster's mean (an empty cluster
+ * keeps its centre), until no label changes or after `iters` rounds.
+ * labels[n] (host, may be NULL) receives the clusters; *modularity the
+ * modularity of the clustering on the context's graph, sum_c [e_c / nnz -
+ * (D_c / nnz)^2] with e_c the CSR entries inside cluster c and D_c its summed
+ * degree; *rounds (may be NULL) the rounds run.  Synchronous.
+ */
+f2v_status f2v_eval_kmeans(f2v_ctx *ctx, int32_t k, const int32_t *init, int32_t iters,
+                           int32_t *labels, double *modularity, int32_t *rounds);
+
 /* Walks the device draws in epoch `epoch` (contexts made by f2v_create_rw):
    out[u*walk_length + i] is the vertex step i of u's walk reaches, or -1
    where the step exerts no force (u has no neighbours, the walk has

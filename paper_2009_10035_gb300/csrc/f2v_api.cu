@@ -391,6 +391,38 @@ std::string global_error() { return g_last_error; }
 
 namespace {
 
+// Device scratch of one synchronous call, freed on every return path.
+struct Scratch {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : st(s) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t count)
+    {
+        void *q = nullptr;
+        cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(count * sizeof(T), 16), st);
+        if (e == cudaSuccess) ptrs.push_back(q);
+        *p = static_cast<T *>(q);
+        return e;
+    }
+    ~Scratch()
+    {
+        for (void *q : ptrs) cudaFreeAsync(q, st);
+        cudaStreamSynchronize(st);
+    }
+};
+
+bool pairs_in_range(const int32_t *pairs, int64_t np, int32_t n)
+{
+    for (int64_t i = 0; i < 2 * np; ++i)
+        if (pairs[i] < 0 || pairs[i] >= n) return false;
+    return true;
+}
+
+}  // namespace
+
+namespace {
+
 double lr_for_epoch(const f2v_ctx *c, int e)
 {
     if (c->schedule == F2V_LR_LINEAR && c->total_epochs > 0)
@@ -1242,6 +1274,147 @@ f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t c
                                   ctx->stream));
     F2V_CUDA(ctx, cudaFreeAsync(dbuf, ctx->stream));
     F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return F2V_OK;
+}
+
+f2v_status f2v_eval_link_lr(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
+                            const int32_t *neg_pairs, int64_t nneg, const uint8_t *train_mask,
+                            double *accuracy, double *theta)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!accuracy || !train_mask) return fail(ctx, F2V_EINVAL, "null argument");
+    if (npos < 0 || nneg < 0 || (npos > 0 && !pos_pairs) || (nneg > 0 && !neg_pairs))
+        return fail(ctx, F2V_EINVAL, "bad pair lists");
+    if (!pairs_in_range(pos_pairs, npos, ctx->n) || !pairs_in_range(neg_pairs, nneg, ctx->n))
+        return fail(ctx, F2V_EINVAL, "a pair names a vertex out of range");
+    if (lr_smem_bytes(ctx->d) > 227 * 1024)
+        return fail(ctx, F2V_EINVAL, "link prediction needs d <= 150 (d = %d)", ctx->d);
+    const int64_t total = npos + nneg;
+    std::vector<int64_t> tr, te;
+    for (int64_t i = 0; i < total; ++i) (train_mask[i] ? tr : te).push_back(i);
+    if (tr.empty() || te.empty())
+        return fail(ctx, F2V_EINVAL, "need at least one training and one test pair");
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    const float *zf = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    const int D1 = ctx->d + 1;
+    Scratch sc(ctx->stream);
+    int32_t *dpos = nullptr, *dneg = nullptr;
+    int64_t *dtr = nullptr, *dte = nullptr;
+    double *dth = nullptr, *dg = nullptr, *dH = nullptr, *dstep = nullptr;
+    unsigned long long *dcorrect = nullptr;
+    cudaError_t e = sc.get(&dpos, 2 * (size_t)npos);
+    if (e == cudaSuccess) e = sc.get(&dneg, 2 * (size_t)nneg);
+    if (e == cudaSuccess) e = sc.get(&dtr, tr.size());
+    if (e == cudaSuccess) e = sc.get(&dte, te.size());
+    if (e == cudaSuccess) e = sc.get(&dth, (size_t)D1);
+    if (e == cudaSuccess) e = sc.get(&dg, (size_t)D1);
+    if (e == cudaSuccess) e = sc.get(&dH, (size_t)D1 * D1);
+    if (e == cudaSuccess) e = sc.get(&dstep, 1);
+    if (e == cudaSuccess) e = sc.get(&dcorrect, 1);
+    if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "eval_link_lr: %s", cudaGetErrorString(e));
+    if (npos)
+        F2V_CUDA(ctx, cudaMemcpyAsync(dpos, pos_pairs, sizeof(int32_t) * 2 * npos,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    if (nneg)
+        F2V_CUDA(ctx, cudaMemcpyAsync(dneg, neg_pairs, sizeof(int32_t) * 2 * nneg,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    F2V_CUDA(ctx, cudaMemcpyAsync(dtr, tr.data(), sizeof(int64_t) * tr.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    F2V_CUDA(ctx, cudaMemcpyAsync(dte, te.data(), sizeof(int64_t) * te.size(),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    F2V_CUDA(ctx, cudaMemsetAsync(dth, 0, sizeof(double) * D1, ctx->stream));
+    for (int it = 0; it < 100; ++it) {   // Newton steps
+        F2V_CUDA(ctx, cudaMemsetAsync(dg, 0, sizeof(double) * D1, ctx->stream));
+        F2V_CUDA(ctx, cudaMemsetAsync(dH, 0, sizeof(double) * D1 * D1, ctx->stream));
+        F2V_CUDA(ctx, launch_lr_newton(zf, ctx->d, dpos, npos, dneg, dtr, (int64_t)tr.size(), dth,
+                                       dg, dH, ctx->stream));
+        F2V_CUDA(ctx, launch_lr_solve(ctx->d, dH, dg, dth, dstep, ctx->stream));
+        ctx->launches += 2;
+        double step = 0.0;
+        F2V_CUDA(ctx, cudaMemcpyAsync(&step, dstep, sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (!(step >= 1e-10)) break;      // converged (or not a number)
+    }
+    F2V_CUDA(ctx, cudaMemsetAsync(dcorrect, 0, sizeof(unsigned long long), ctx->stream));
+    F2V_CUDA(ctx, launch_lr_accuracy(zf, ctx->d, dpos, npos, dneg, dte, (int64_t)te.size(), dth,
+                                     dcorrect, ctx->stream));
+    ctx->launches++;
+    unsigned long long correct = 0;
+    F2V_CUDA(ctx, cudaMemcpyAsync(&correct, dcorrect, sizeof(correct), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    if (theta)
+        F2V_CUDA(ctx, cudaMemcpyAsync(theta, dth, sizeof(double) * D1, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *accuracy = (double)correct / (double)te.size();
+    return F2V_OK;
+}
+
+f2v_status f2v_eval_kmeans(f2v_ctx *ctx, int32_t k, const int32_t *init, int32_t iters,
+                           int32_t *labels, double *modularity, int32_t *rounds)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!init || !modularity) return fail(ctx, F2V_EINVAL, "null argument");
+    if (k < 1 || k > 64) return fail(ctx, F2V_EINVAL, "k = %d, must be in [1, 64]", k);
+    if (ctx->d > 256) return fail(ctx, F2V_EINVAL, "k-means needs d <= 256 (d = %d)", ctx->d);
+    if (iters < 1) return fail(ctx, F2V_EINVAL, "iters = %d < 1", iters);
+    for (int c = 0; c < k; ++c)
+        if (init[c] < 0 || init[c] >= ctx->n)
+            return fail(ctx, F2V_EINVAL, "init[%d] out of range", c);
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    const float *zf = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    const int32_t n = ctx->n, d = ctx->d;
+    Scratch sc(ctx->stream);
+    int32_t *dinit = nullptr, *dlab = nullptr;
+    double *dC = nullptr, *dsum = nullptr, *dq = nullptr;
+    unsigned long long *dcnt = nullptr, *dchg = nullptr, *de = nullptr, *dD = nullptr;
+    cudaError_t e = sc.get(&dinit, (size_t)k);
+    if (e == cudaSuccess) e = sc.get(&dlab, (size_t)n);
+    if (e == cudaSuccess) e = sc.get(&dC, (size_t)k * d);
+    if (e == cudaSuccess) e = sc.get(&dsum, (size_t)k * d);
+    if (e == cudaSuccess) e = sc.get(&dq, 1);
+    if (e == cudaSuccess) e = sc.get(&dcnt, (size_t)k);
+    if (e == cudaSuccess) e = sc.get(&dchg, 1);
+    if (e == cudaSuccess) e = sc.get(&de, (size_t)k);
+    if (e == cudaSuccess) e = sc.get(&dD, (size_t)k);
+    if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "eval_kmeans: %s", cudaGetErrorString(e));
+    F2V_CUDA(ctx, cudaMemcpyAsync(dinit, init, sizeof(int32_t) * k, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    F2V_CUDA(ctx, launch_km_init(zf, d, dinit, k, dC, ctx->stream));
+    F2V_CUDA(ctx, cudaMemsetAsync(dlab, 0xFF, sizeof(int32_t) * n, ctx->stream));
+    ctx->launches++;
+    int it = 0;
+    for (it = 1; it <= iters; ++it) {   // Lloyd rounds
+        F2V_CUDA(ctx, cudaMemsetAsync(dsum, 0, sizeof(double) * k * d, ctx->stream));
+        F2V_CUDA(ctx, cudaMemsetAsync(dcnt, 0, sizeof(unsigned long long) * k, ctx->stream));
+        F2V_CUDA(ctx, cudaMemsetAsync(dchg, 0, sizeof(unsigned long long), ctx->stream));
+        F2V_CUDA(ctx, launch_km_assign(zf, n, d, dC, k, dlab, dsum, dcnt, dchg, ctx->stream));
+        ctx->launches++;
+        unsigned long long changed = 0;
+        F2V_CUDA(ctx, cudaMemcpyAsync(&changed, dchg, sizeof(changed), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (changed == 0) break;
+        F2V_CUDA(ctx, launch_km_update(k, d, dsum, dcnt, dC, ctx->stream));
+        ctx->launches++;
+    }
+    F2V_CUDA(ctx, cudaMemsetAsync(de, 0, sizeof(unsigned long long) * k, ctx->stream));
+    F2V_CUDA(ctx, cudaMemsetAsync(dD, 0, sizeof(unsigned long long) * k, ctx->stream));
+    F2V_CUDA(ctx, launch_modularity(ctx->row_ptr0, ctx->col_idx0, n, ctx->nnz, dlab, k, de, dD,
+                                    dq, ctx->stream));
+    ctx->launches += 2;
+    F2V_CUDA(ctx, cudaMemcpyAsync(modularity, dq, sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    if (labels)
+        F2V_CUDA(ctx, cudaMemcpyAsync(labels, dlab, sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    F2V_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (rounds) *rounds = std::min(it, iters);
     return F2V_OK;
 }
 

@@ -158,6 +158,28 @@ cudaError_t launch_mb_tables(const int64_t *apair2, int32_t n, int32_t b, int32_
 cudaError_t launch_permute_rows(const float *src, float *dst, const int32_t *perm, int64_t rows,
                                 int32_t d, bool scatter, cudaStream_t st);
 
+// Downstream evaluations of Sec. IV (f2v_downstream.cu), FP64.
+size_t lr_smem_bytes(int32_t d);
+cudaError_t launch_lr_newton(const float *z, int32_t d, const int32_t *pos, int64_t npos,
+                             const int32_t *neg, const int64_t *idx, int64_t m,
+                             const double *theta, double *g, double *H, cudaStream_t st);
+cudaError_t launch_lr_solve(int32_t d, double *H, double *g, double *theta, double *step_max,
+                            cudaStream_t st);
+cudaError_t launch_lr_accuracy(const float *z, int32_t d, const int32_t *pos, int64_t npos,
+                               const int32_t *neg, const int64_t *idx, int64_t m,
+                               const double *theta, unsigned long long *correct, cudaStream_t st);
+cudaError_t launch_km_init(const float *z, int32_t d, const int32_t *init, int32_t k, double *C,
+                           cudaStream_t st);
+cudaError_t launch_km_assign(const float *z, int32_t n, int32_t d, const double *C, int32_t k,
+                             int32_t *labels, double *sums, unsigned long long *counts,
+                             unsigned long long *changed, cudaStream_t st);
+cudaError_t launch_km_update(int32_t k, int32_t d, const double *sums,
+                             const unsigned long long *counts, double *C, cudaStream_t st);
+cudaError_t launch_modularity(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                              int64_t nnz, const int32_t *labels, int32_t k,
+                              unsigned long long *e, unsigned long long *D, double *q,
+                              cudaStream_t st);
+
 // out[u * walk + i]: the code of walk step i of vertex u in the list
 // `partner` (kPartnerNone for a vertex without neighbours).
 cudaError_t launch_extract_walks(const int64_t *apair, const int32_t *row_ptr, int32_t n,

@@ -95,6 +95,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
             "f2v_debug_samples": ([vp, i32, vp, sz], st),
             "f2v_debug_walks": ([vp, i32, vp, sz], st),
+            "f2v_eval_link_lr": ([vp, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_double),
+                                  vp], st),
+            "f2v_eval_kmeans": ([vp, i32, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(i32)], st),
             "f2v_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
             "f2v_device_bytes": ([vp, ctypes.POINTER(sz)], st),
             "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
@@ -286,6 +290,33 @@ class Context:
         buf = out if out.size else np.zeros(1, np.int32)
         self._check(self._lib.f2v_debug_samples(self._h, int(epoch), _ptr(buf), out.size))
         return out
+
+    def eval_link_lr(self, pos_pairs, neg_pairs, train_mask):
+        """Sec. IV link prediction: Hadamard features, logistic regression
+        fitted on train_mask (pos pairs first), accuracy on the rest.
+        Returns (accuracy, theta = (w, b))."""
+        pos = np.ascontiguousarray(pos_pairs, dtype=np.int32).reshape(-1, 2)
+        neg = np.ascontiguousarray(neg_pairs, dtype=np.int32).reshape(-1, 2)
+        mask = np.ascontiguousarray(train_mask, dtype=np.uint8)
+        if mask.size != pos.shape[0] + neg.shape[0]:
+            raise ValueError("train_mask must have one entry per pair")
+        acc = ctypes.c_double()
+        theta = np.zeros(self.d + 1, dtype=np.float64)
+        self._check(self._lib.f2v_eval_link_lr(self._h, _ptr(pos), pos.shape[0], _ptr(neg),
+                                               neg.shape[0], _ptr(mask), ctypes.byref(acc),
+                                               _ptr(theta)))
+        return acc.value, theta
+
+    def eval_kmeans(self, init, iters: int = 100):
+        """Sec. IV clustering: k-means from centres Z[init]; returns
+        (modularity, labels, rounds)."""
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        labels = np.zeros(self.n, dtype=np.int32)
+        q = ctypes.c_double()
+        r = ctypes.c_int32()
+        self._check(self._lib.f2v_eval_kmeans(self._h, init.size, _ptr(init), int(iters),
+                                              _ptr(labels), ctypes.byref(q), ctypes.byref(r)))
+        return q.value, labels, r.value
 
     def debug_walks(self, epoch: int) -> np.ndarray:
         """n x walk_length: the vertex each walk step reaches, -1 where the

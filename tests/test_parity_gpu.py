@@ -729,3 +729,75 @@ def test_rmat_scale20_d128_partition(model, rmat20):
     worst = check_partition_steps(g, 128, model, 5, b, lr=0.02, seed=1, epochs=1,
                                   steps={(0, 0), (0, M // 2), (0, M - 1)})
     print(f"rmat20 partition model={model}: worst scaled error {worst:.3e}")
+
+
+# ---------------------------------------------------------------- Sec. IV evaluations
+
+from oracle import downstream as ds  # noqa: E402
+
+
+def _trained(g, d=32, epochs=3, model=f2v.TDIST, seed=1):
+    ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=5, lr=0.02, minibatch=128,
+                      seed=seed)
+    ctx.train(epochs)
+    return ctx
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_link_prediction_matches_oracle(model):
+    """Hadamard features + logistic regression on a 50/50 split: the fitted
+    theta against the FP64 oracle's Newton fit on the GPU's own Z, and the
+    accuracy counted the same way."""
+    g = graphs.holdout(graphs.sbm(2000, 8, 0.05, 0.002, seed=3), frac=0.1, seed=5)
+    with _trained(g, model=model) as ctx:
+        Z = ctx.embedding().astype(np.float64)
+        npos = g.test_pos.shape[0]
+        mask = np.random.default_rng(7).random(npos + g.test_neg.shape[0]) < 0.5
+        acc, theta = ctx.eval_link_lr(g.test_pos, g.test_neg, mask)
+    acc_o, w_o, b_o = ds.link_accuracy(Z, g.test_pos, g.test_neg, mask)
+    np.testing.assert_allclose(theta[:-1], w_o, rtol=1e-8, atol=1e-9)
+    assert theta[-1] == pytest.approx(b_o, rel=1e-8, abs=1e-9)
+    assert abs(acc - acc_o) <= 1.0 / (~mask).sum()    # at most one boundary pair
+    assert acc > 0.6
+
+
+@pytest.mark.parametrize("k", [2, 8, 20])
+def test_kmeans_and_modularity_match_oracle(k):
+    g = graphs.sbm(3000, 8, 0.05, 0.002, seed=4)
+    init = np.random.default_rng(k).choice(g.n, k, replace=False)
+    with _trained(g, d=32, epochs=5) as ctx:
+        Z = ctx.embedding().astype(np.float64)
+        q, labels, rounds = ctx.eval_kmeans(init, iters=60)
+    want, C, it = ds.kmeans(Z, init, iters=60)
+    # labels may differ only where the two nearest centres tie to rounding
+    diff = np.flatnonzero(labels != want)
+    if diff.size:
+        d2 = ((Z[diff, None, :] - C[None, :, :]) ** 2).sum(axis=2)
+        two = np.sort(d2, axis=1)[:, :2]
+        assert (two[:, 1] - two[:, 0] <= 1e-9 * two[:, 1]).all()
+    assert diff.size <= 2
+    assert rounds == it
+    assert q == pytest.approx(ds.modularity(g.row_ptr, g.col_idx, labels), abs=1e-12)
+
+
+def test_kmeans_recovers_planted_communities():
+    # the SBM's blocks are the communities: the best k-means clustering of a
+    # trained t-model embedding scores near the planted partition's modularity
+    g = graphs.sbm(4000, 4, 0.03, 0.0005, seed=6)
+    blocks = np.repeat(np.arange(4), 1000)
+    with _trained(g, d=16, epochs=20) as ctx:
+        best = max(ctx.eval_kmeans(np.random.default_rng(s).choice(g.n, 4, replace=False))[0]
+                   for s in range(3))
+    planted = ds.modularity(g.row_ptr, g.col_idx, blocks)
+    assert best >= 0.9 * planted, (best, planted)
+
+
+def test_evaluations_reject_bad_arguments():
+    g = graphs.erdos_renyi(100, p=0.05, seed=1)
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 8, s=2, minibatch=50, seed=1) as ctx:
+        with pytest.raises(f2v.F2VError):
+            ctx.eval_kmeans(np.arange(65))
+        with pytest.raises(f2v.F2VError):
+            ctx.eval_kmeans([0, 100])
+        with pytest.raises(f2v.F2VError):
+            ctx.eval_link_lr([[0, 1]], [[0, 2]], [1, 1])       # no test pair
