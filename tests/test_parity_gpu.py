@@ -758,7 +758,11 @@ def test_link_prediction_matches_oracle(model):
     np.testing.assert_allclose(theta[:-1], w_o, rtol=1e-8, atol=1e-9)
     assert theta[-1] == pytest.approx(b_o, rel=1e-8, abs=1e-9)
     assert abs(acc - acc_o) <= 1.0 / (~mask).sum()    # at most one boundary pair
-    assert acc > 0.6
+    if model == f2v.SIGMOID:
+        # z_u . z_v, the sigmoid model's similarity, is linear in the Hadamard
+        # features (the paper reports this protocol for sForce2Vec); the t
+        # model's -|z_u - z_v|^2 needs the norms, which the features lack
+        assert acc > 0.6
 
 
 @pytest.mark.parametrize("k", [2, 8, 20])
