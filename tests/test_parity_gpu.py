@@ -736,8 +736,8 @@ def test_rmat_scale20_d128_partition(model, rmat20):
 from oracle import downstream as ds  # noqa: E402
 
 
-def _trained(g, d=32, epochs=3, model=f2v.TDIST, seed=1):
-    ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=5, lr=0.02, minibatch=128,
+def _trained(g, d=32, epochs=3, model=f2v.TDIST, seed=1, lr=0.02):
+    ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=5, lr=lr, minibatch=128,
                       seed=seed)
     ctx.train(epochs)
     return ctx
@@ -749,7 +749,7 @@ def test_link_prediction_matches_oracle(model):
     theta against the FP64 oracle's Newton fit on the GPU's own Z, and the
     accuracy counted the same way."""
     g = graphs.holdout(graphs.sbm(2000, 8, 0.05, 0.002, seed=3), frac=0.1, seed=5)
-    with _trained(g, model=model) as ctx:
+    with _trained(g, d=16, epochs=40, model=model, lr=0.05) as ctx:
         Z = ctx.embedding().astype(np.float64)
         npos = g.test_pos.shape[0]
         mask = np.random.default_rng(7).random(npos + g.test_neg.shape[0]) < 0.5
@@ -758,11 +758,9 @@ def test_link_prediction_matches_oracle(model):
     np.testing.assert_allclose(theta[:-1], w_o, rtol=1e-8, atol=1e-9)
     assert theta[-1] == pytest.approx(b_o, rel=1e-8, abs=1e-9)
     assert abs(acc - acc_o) <= 1.0 / (~mask).sum()    # at most one boundary pair
-    if model == f2v.SIGMOID:
-        # z_u . z_v, the sigmoid model's similarity, is linear in the Hadamard
-        # features (the paper reports this protocol for sForce2Vec); the t
-        # model's -|z_u - z_v|^2 needs the norms, which the features lack
-        assert acc > 0.6
+    # held-out edges are predicted (the FP64 oracle trained the same way
+    # reaches 0.66 with the sigmoid model and 0.81 with the t model)
+    assert acc > 0.6
 
 
 @pytest.mark.parametrize("k", [2, 8, 20])
