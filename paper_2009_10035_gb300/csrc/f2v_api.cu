@@ -344,9 +344,9 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
         const int u0 = k * c->b, u1 = std::min(n, u0 + c->b);
         const int64_t P0 = c->h_apair[(size_t)u0], P1 = c->h_apair[(size_t)u1];
         int64_t C = c->C;
-        if (c->bulk) {   // one chunk per warp, a multiple of 32 pairs
+        if (c->bulk) {   // two chunks per warp, a multiple of 32 pairs
             C = (P1 - P0 + W - 1) / W;
-            C = std::max<int64_t>(32, (C + 31) / 32 * 32);
+            C = std::max<int64_t>(32, ((C + 1) / 2 + 31) / 32 * 32);
         }
         if (P1 - P0 >= (int64_t)INT32_MAX - C) return false;
         c->mb_C[(size_t)k] = (int32_t)C;
@@ -372,7 +372,8 @@ bool build_schedule(f2v_ctx *c, const int32_t *row_ptr, std::vector<int32_t> &it
         int64_t maxPk = 0;
         for (size_t i = 0; i < top; ++i) maxPk += cnt[i];
         if (maxPk >= (int64_t)INT32_MAX - 32) return false;
-        const int64_t worst = c->bulk ? std::max<int64_t>(W, 1) : (maxPk + c->C - 1) / c->C;
+        // (the staged kernel cuts a minibatch into at most two chunks per warp)
+        const int64_t worst = c->bulk ? std::max<int64_t>(2 * W, 1) : (maxPk + c->C - 1) / c->C;
         c->max_items = std::max(c->max_items, worst);
     }
     return true;

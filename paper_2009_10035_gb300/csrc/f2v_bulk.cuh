@@ -4,7 +4,7 @@
 //
 // Work.  Minibatch k's pair sequence (neighbours of each vertex in CSR
 // order, then its s negative samples) is cut into chunks of C_k pairs (about
-// one per warp); a free warp takes the next unclaimed chunk of the oldest
+// two per warp); a free warp takes the next unclaimed chunk of the oldest
 // minibatch that has one left, so warps flow from one minibatch into the next
 // without a grid-wide barrier, and a slow chunk holds up no warp but its own.
 // Per tile of at most 32 pairs spanning at most 8 vertices:

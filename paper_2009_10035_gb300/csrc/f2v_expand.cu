@@ -40,7 +40,21 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
         const int64_t base = apair[u];
         const int32_t r0 = row_ptr[u];
         const int32_t deg = row_ptr[u + 1] - r0;
-        for (int32_t j = lane; j < deg; j += 32) partner[base + j] = col_idx[r0 + j];
+        // eight loads in flight per lane before their stores (a hub's row is
+        // one warp's: tens of thousands of entries)
+        for (int32_t j0 = 0; j0 < deg; j0 += 32 * 8) {
+            int32_t v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int32_t j = j0 + 32 * t + lane;
+                v[t] = (j < deg) ? col_idx[r0 + j] : 0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int32_t j = j0 + 32 * t + lane;
+                if (j < deg) partner[base + j] = v[t];
+            }
+        }
         const int64_t uo = perm ? perm[u] : u;                // the original id
         const int64_t kb = shared_b > 0 ? u / shared_b : -1;   // u's minibatch
         for (int32_t k = lane; k < s; k += 32) {

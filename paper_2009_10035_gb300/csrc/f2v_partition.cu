@@ -88,7 +88,22 @@ __global__ void part_cols_kernel(const int32_t *__restrict__ row_ptr,
     for (int64_t p = warp; p < n; p += nwarps) {
         const int32_t u = perm[p];
         const int32_t lo = row_ptr[u], deg = row_ptr[u + 1] - lo, out = row_ptr2[p];
-        for (int32_t j = lane; j < deg; j += 32) col2[out + j] = rank[col_idx[lo + j]];
+        // eight gathers in flight per lane (a hub's row is one warp's)
+        for (int32_t j0 = 0; j0 < deg; j0 += 32 * 8) {
+            int32_t v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int32_t j = j0 + 32 * t + lane;
+                v[t] = (j < deg) ? col_idx[lo + j] : 0;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = rank[v[t]];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int32_t j = j0 + 32 * t + lane;
+                if (j < deg) col2[out + j] = v[t];
+            }
+        }
     }
 }
 
@@ -106,9 +121,9 @@ __global__ void part_sizes_kernel(const int64_t *__restrict__ apair, int32_t n, 
         const int64_t u0 = k * (int64_t)b, u1 = min((int64_t)n, u0 + b);
         const int64_t Pk = apair[u1] - apair[u0];
         int64_t C = Cfix;
-        if (W > 0) {   // staged kernel: one chunk per warp, a multiple of 32 pairs
+        if (W > 0) {   // staged kernel: two chunks per warp, a multiple of 32 pairs
             C = (Pk + W - 1) / W;
-            C = max((int64_t)32, (C + 31) / 32 * 32);
+            C = max((int64_t)32, ((C + 1) / 2 + 31) / 32 * 32);
         }
         mb_C[k] = (int32_t)C;
         nch[k] = (Pk + C - 1) / C;
