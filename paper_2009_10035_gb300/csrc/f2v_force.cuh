@@ -513,24 +513,33 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
                 if (kr[i] != KIND_NONE)
                     load_partner<L, VEC, NV, EXACT, COHERENT>(a, v, gl, zv[i]);
             }
+            // the U rows in phases, so that their independent work overlaps:
+            // partial sums, the group reductions level by level, the force
+            // scalars; then the accumulation, in row order
+            float part[U];
 #pragma unroll
             for (int i = 0; i < U; ++i) {
-                if (kr[i] == KIND_NONE) continue;
-                float part = 0.f;
+                part[i] = 0.f;
                 if (dist) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         const float df = zu[e] - zv[i][e];
-                        part = fmaf(df, df, part);
+                        part[i] = fmaf(df, df, part[i]);
                     }
                 } else {
 #pragma unroll
-                    for (int e = 0; e < E; ++e) part = fmaf(zu[e], zv[i][e], part);
+                    for (int e = 0; e < E; ++e) part[i] = fmaf(zu[e], zv[i][e], part[i]);
                 }
+            }
 #pragma unroll
-                for (int m = L / 2; m >= 1; m >>= 1)
-                    part += __shfl_xor_sync(gmask, part, m, L);
-                const float coef = pair_coef(model, kr[i], part);
+            for (int m = L / 2; m >= 1; m >>= 1) {
+#pragma unroll
+                for (int i = 0; i < U; ++i) part[i] += __shfl_xor_sync(gmask, part[i], m, L);
+            }
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                if (kr[i] == KIND_NONE) continue;     // (its row was not loaded)
+                const float coef = pair_coef(model, kr[i], part[i]);
                 if (dist) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
