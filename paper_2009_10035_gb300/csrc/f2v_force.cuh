@@ -536,10 +536,22 @@ __device__ __forceinline__ void force_item(const ForceArgs<Ts> &a, const FinishC
 #pragma unroll
                 for (int i = 0; i < U; ++i) part[i] += __shfl_xor_sync(gmask, part[i], m, L);
             }
+            // lane i of the group turns row i's sum into its scalar once (after
+            // the butterfly every lane holds the same sum, bit for bit) and the
+            // group shares the U scalars
+            float my_part = part[0];
+            int my_kind = kr[0];
+#pragma unroll
+            for (int i = 1; i < U; ++i)
+                if (gl == i) {
+                    my_part = part[i];
+                    my_kind = kr[i];
+                }
+            const float my_coef = (my_kind != KIND_NONE) ? pair_coef(model, my_kind, my_part) : 0.f;
 #pragma unroll
             for (int i = 0; i < U; ++i) {
+                const float coef = __shfl_sync(gmask, my_coef, i, L);
                 if (kr[i] == KIND_NONE) continue;     // (its row was not loaded)
-                const float coef = pair_coef(model, kr[i], part[i]);
                 if (dist) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) g[e] = fmaf(coef, zu[e] - zv[i][e], g[e]);
