@@ -18,6 +18,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
+#include <thread>
 #include <vector>
 
 #include "f2v.h"
@@ -282,17 +285,64 @@ f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_
             return fail(nullptr, F2V_EINVAL, "row_ptr not monotone at row %d", u);
     const int64_t nnz = row_ptr[n];
     if (nnz > 0 && !col_idx) return fail(nullptr, F2V_EINVAL, "col_idx is NULL");
-    std::vector<int32_t> stamp((size_t)n, -1);
-    for (int32_t u = 0; u < n; ++u) {
-        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-            const int32_t v = col_idx[e];
-            if (v < 0 || v >= n)
-                return fail(nullptr, F2V_EINVAL, "col_idx[%d] = %d out of range [0, %d)", e, v, n);
-            if (v == u) return fail(nullptr, F2V_EINVAL, "self-loop at vertex %d", u);
-            if (stamp[(size_t)v] == u)
-                return fail(nullptr, F2V_EINVAL, "duplicate entry (%d, %d)", u, v);
-            stamp[(size_t)v] = u;
+    // Rows are checked in parallel ranges of about equal entries.  A row whose
+    // columns strictly increase has no duplicate (a sequential test); only
+    // other rows need the per-thread stamp array.  The first bad row found in
+    // row order is the one reported.
+    const int nthreads = (int)std::max<int64_t>(
+        1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16,
+                              (nnz + n) / 65536 + 1}));
+    std::vector<int32_t> bad_row((size_t)nthreads, INT32_MAX), bad_kind((size_t)nthreads, 0);
+    std::vector<int32_t> bounds((size_t)nthreads + 1, n);
+    bounds[0] = 0;
+    for (int t = 1; t < nthreads; ++t) {   // split by entries
+        const int64_t target = nnz * t / nthreads;
+        bounds[(size_t)t] = (int32_t)(std::upper_bound(row_ptr, row_ptr + n + 1, (int32_t)target) -
+                                      row_ptr - 1);
+        bounds[(size_t)t] = std::max(bounds[(size_t)t], bounds[(size_t)t - 1]);
+    }
+    auto check_range = [&](int t) {
+        std::vector<int32_t> stamp;
+        for (int32_t u = bounds[(size_t)t]; u < bounds[(size_t)t + 1]; ++u) {
+            const int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
+            bool sorted = true;
+            for (int32_t e = lo; e < hi; ++e) {
+                const int32_t v = col_idx[e];
+                if (v < 0 || v >= n || v == u) {
+                    bad_row[(size_t)t] = u;
+                    bad_kind[(size_t)t] = (v == u) ? 2 : 1;
+                    return;
+                }
+                if (e > lo && v <= col_idx[e - 1]) sorted = false;
+            }
+            if (sorted) continue;
+            if (stamp.empty()) stamp.assign((size_t)n, -1);
+            for (int32_t e = lo; e < hi; ++e) {
+                if (stamp[(size_t)col_idx[e]] == u) {
+                    bad_row[(size_t)t] = u;
+                    bad_kind[(size_t)t] = 3;
+                    return;
+                }
+                stamp[(size_t)col_idx[e]] = u;
+            }
         }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nthreads; ++t) pool.emplace_back(check_range, t);
+        check_range(0);
+        for (auto &th : pool) th.join();
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        if (bad_kind[(size_t)t] == 0) continue;
+        const int32_t u = bad_row[(size_t)t];
+        if (bad_kind[(size_t)t] == 2) return fail(nullptr, F2V_EINVAL, "self-loop at vertex %d", u);
+        if (bad_kind[(size_t)t] == 3)
+            return fail(nullptr, F2V_EINVAL, "duplicate entry in row %d", u);
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (col_idx[e] < 0 || col_idx[e] >= n)
+                return fail(nullptr, F2V_EINVAL, "col_idx[%d] = %d out of range [0, %d)", e,
+                            col_idx[e], n);
     }
     if (flags & F2V_FLAG_CHECK_SYMMETRY) {
         // count (u, v) against (v, u): transpose counts must match row by row
