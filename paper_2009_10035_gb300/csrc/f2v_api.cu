@@ -275,23 +275,35 @@ void release(f2v_ctx *c)
 }
 
 // Host-side validation of the CSR (Sec. II-A: 0/1 adjacency, no self-loops).
-f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
-                          uint32_t flags)
+// The checks of f2v_create's CSR, with up to `max_threads` host threads;
+// on failure *msg says why.  Touches no global state (several graphs may be
+// checked at once).
+f2v_status csr_check(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, uint32_t flags,
+                     int max_threads, std::string *msg)
 {
-    if (!row_ptr) return fail(nullptr, F2V_EINVAL, "row_ptr is NULL");
-    if (row_ptr[0] != 0) return fail(nullptr, F2V_EINVAL, "row_ptr[0] = %d, expected 0", row_ptr[0]);
+    auto bad = [&](const char *fmt, ...) {
+        char buf[256];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        *msg = buf;
+        return F2V_EINVAL;
+    };
+    if (!row_ptr) return bad("row_ptr is NULL");
+    if (row_ptr[0] != 0) return bad("row_ptr[0] = %d, expected 0", row_ptr[0]);
     for (int32_t u = 0; u < n; ++u)
         if (row_ptr[u + 1] < row_ptr[u])
-            return fail(nullptr, F2V_EINVAL, "row_ptr not monotone at row %d", u);
+            return bad("row_ptr not monotone at row %d", u);
     const int64_t nnz = row_ptr[n];
-    if (nnz > 0 && !col_idx) return fail(nullptr, F2V_EINVAL, "col_idx is NULL");
+    if (nnz > 0 && !col_idx) return bad("col_idx is NULL");
     // Rows are checked in parallel ranges of about equal entries.  A row whose
     // columns strictly increase has no duplicate (a sequential test); only
     // other rows need the per-thread stamp array.  The first bad row found in
     // row order is the one reported.
     const int nthreads = (int)std::max<int64_t>(
-        1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(), 16,
-                              (nnz + n) / 65536 + 1}));
+        1, std::min<int64_t>({(int64_t)std::thread::hardware_concurrency(),
+                              (int64_t)max_threads, (nnz + n) / 65536 + 1}));
     std::vector<int32_t> bad_row((size_t)nthreads, INT32_MAX), bad_kind((size_t)nthreads, 0);
     std::vector<int32_t> bounds((size_t)nthreads + 1, n);
     bounds[0] = 0;
@@ -336,12 +348,12 @@ f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_
     for (int t = 0; t < nthreads; ++t) {
         if (bad_kind[(size_t)t] == 0) continue;
         const int32_t u = bad_row[(size_t)t];
-        if (bad_kind[(size_t)t] == 2) return fail(nullptr, F2V_EINVAL, "self-loop at vertex %d", u);
+        if (bad_kind[(size_t)t] == 2) return bad("self-loop at vertex %d", u);
         if (bad_kind[(size_t)t] == 3)
-            return fail(nullptr, F2V_EINVAL, "duplicate entry in row %d", u);
+            return bad("duplicate entry in row %d", u);
         for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
             if (col_idx[e] < 0 || col_idx[e] >= n)
-                return fail(nullptr, F2V_EINVAL, "col_idx[%d] = %d out of range [0, %d)", e,
+                return bad("col_idx[%d] = %d out of range [0, %d)", e,
                             col_idx[e], n);
     }
     if (flags & F2V_FLAG_CHECK_SYMMETRY) {
@@ -350,7 +362,7 @@ f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_
         for (int64_t e = 0; e < nnz; ++e) tcount[(size_t)col_idx[e] + 1]++;
         for (int32_t u = 0; u < n; ++u)
             if (tcount[(size_t)u + 1] != row_ptr[u + 1] - row_ptr[u])
-                return fail(nullptr, F2V_EINVAL, "CSR not symmetric (row %d)", u);
+                return bad("CSR not symmetric (row %d)", u);
         for (int32_t u = 0; u < n; ++u) tcount[(size_t)u + 1] += tcount[(size_t)u];
         std::vector<int32_t> tcol((size_t)nnz);
         std::vector<int64_t> fill(tcount.begin(), tcount.end() - 1);
@@ -363,9 +375,18 @@ f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_
                                    tcol.begin() + tcount[(size_t)u + 1]);
             std::sort(a.begin(), a.end());
             std::sort(b.begin(), b.end());
-            if (a != b) return fail(nullptr, F2V_EINVAL, "CSR not symmetric (row %d)", u);
+            if (a != b) return bad("CSR not symmetric (row %d)", u);
         }
     }
+    return F2V_OK;
+}
+
+f2v_status validate_graph(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                          uint32_t flags)
+{
+    std::string msg;
+    const f2v_status st = csr_check(row_ptr, col_idx, n, flags, 16, &msg);
+    if (st != F2V_OK) return fail(nullptr, st, "%s", msg.c_str());
     return F2V_OK;
 }
 
@@ -435,6 +456,11 @@ namespace f2v {
 f2v_status check_csr(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, uint32_t flags)
 {
     return validate_graph(row_ptr, col_idx, n, flags);
+}
+f2v_status check_csr_quiet(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                           uint32_t flags, int max_threads, std::string *msg)
+{
+    return csr_check(row_ptr, col_idx, n, flags, max_threads, msg);
 }
 void set_global_error(const std::string &msg) { g_last_error = msg; }
 std::string global_error() { return g_last_error; }

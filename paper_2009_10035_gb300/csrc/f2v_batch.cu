@@ -10,7 +10,11 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <atomic>
+#include <string>
+#include <thread>
 #include <utility>
+#include <vector>
 
 #include "f2v.h"
 #include "f2v_batch.h"
@@ -1028,16 +1032,45 @@ f2v_status f2v_batch_create(int32_t num_graphs, const int32_t *n, const int32_t 
         delete b;
         return st;
     }
+    // offsets of every graph, then every CSR checked, graphs spread over the
+    // host threads (one thread per graph)
+    std::vector<int64_t> roffs((size_t)num_graphs + 1, 0), coffs((size_t)num_graphs + 1, 0);
+    for (int g = 0; g < num_graphs; ++g) {
+        roffs[(size_t)g + 1] = roffs[(size_t)g] + (int64_t)n[g] + 1;
+        coffs[(size_t)g + 1] = coffs[(size_t)g] + row_ptr[roffs[(size_t)g] + n[g]];
+        if (coffs[(size_t)g + 1] > coffs[(size_t)g] && !col_idx) {
+            delete b;
+            return gfail(F2V_EINVAL, "graph %d: col_idx is NULL", g);
+        }
+    }
+    {
+        std::vector<std::string> msgs((size_t)num_graphs);
+        std::vector<f2v_status> sts((size_t)num_graphs, F2V_OK);
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            for (int g; (g = next.fetch_add(1)) < num_graphs;)
+                sts[(size_t)g] = check_csr_quiet(row_ptr + roffs[(size_t)g],
+                                                 col_idx ? col_idx + coffs[(size_t)g] : nullptr,
+                                                 n[g], 0, 1, &msgs[(size_t)g]);
+        };
+        const int nt = (int)std::max<unsigned>(1, std::min<unsigned>(
+                                                       16, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < std::min(nt, num_graphs); ++t) pool.emplace_back(work);
+        work();
+        for (auto &th : pool) th.join();
+        for (int g = 0; g < num_graphs; ++g)
+            if (sts[(size_t)g] != F2V_OK) {
+                delete b;
+                return gfail(sts[(size_t)g], "graph %d: %s", g, msgs[(size_t)g].c_str());
+            }
+    }
     int64_t roff = 0, coff = 0;
     for (int g = 0; g < num_graphs; ++g) {
         const int32_t *rp = row_ptr + roff;
         const int64_t nnz = rp[n[g]];
-        if (nnz > 0 && !col_idx) {
-            delete b;
-            return gfail(F2V_EINVAL, "graph %d: col_idx is NULL", g);
-        }
         const int id = b->eng.add_graph(rp, col_idx ? col_idx + coff : nullptr, n[g], d[g], seed[g],
-                                        lr, 0, 0, &st);
+                                        lr, 0, 0, &st, /*validated=*/true);
         if (id < 0) {
             gfail(st, "graph %d: %s", g, b->eng.err().c_str());
             delete b;

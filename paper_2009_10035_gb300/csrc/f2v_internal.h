@@ -225,6 +225,10 @@ cudaError_t launch_force_bf16(const Shape &sh, const ForceArgs<__nv_bfloat16> &a
 // Host-side checks shared by the entry points (f2v_api.cu): the CSR rules of
 // f2v_create (message in the thread's global error), and that error string.
 f2v_status check_csr(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, uint32_t flags);
+// The same checks with at most max_threads host threads, the reason in *msg
+// and no global state touched (graphs may be checked concurrently).
+f2v_status check_csr_quiet(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                           uint32_t flags, int max_threads, std::string *msg);
 void set_global_error(const std::string &msg);
 std::string global_error();
 
