@@ -321,3 +321,17 @@ def test_full_batched_workload_sampled():
             bt.run_minibatches(1)
             check_step(bt, glist, gb.d, gb.seed, f2v.TDIST, s, b, lr, 0, k, before, list(glist))
         assert bt.progress == (1, 0)
+
+
+def test_batch_create_reports_the_bad_graph():
+    """Graphs are checked concurrently; the error names the first bad one."""
+    gb = graphs.sbm_batch(8, seed=3, n_range=(50, 400))
+    rp = gb.row_ptr.copy()
+    ci = gb.col_idx.copy()
+    # a self-loop in graph 5: its first entry made to point at its own row
+    r0 = int(gb.row_off[5])
+    c0 = int(gb.col_off[5])
+    u = int(np.flatnonzero(np.diff(rp[r0:r0 + gb.n[5] + 1]) > 0)[0])
+    ci[c0 + rp[r0 + u]] = u
+    with pytest.raises(f2v.F2VError, match="graph 5: self-loop"):
+        f2v.Batch(gb.n, gb.d, gb.seed, rp, ci)
