@@ -7,7 +7,7 @@
 // two per warp); a free warp takes the next unclaimed chunk of the oldest
 // minibatch that has one left, so warps flow from one minibatch into the next
 // without a grid-wide barrier, and a slow chunk holds up no warp but its own.
-// Per tile of at most 32 pairs spanning at most 8 vertices:
+// Per tile of at most 32 pairs spanning at most kOwnSlots (4) vertices:
 //   decode  lane t finds pair t's vertex and partner (the epoch's partner list);
 //   stage   TMA gather4 copies bring the tile's partner rows and own rows
 //           into the warp's shared buffers, completing on one mbarrier; the
@@ -45,7 +45,10 @@
 
 namespace f2v {
 
-constexpr int kOwnSlots = 8;                 // distinct vertices per tile at most
+constexpr int kOwnSlots = 4;                 // distinct vertices per tile at most
+// own rows arrive by tile::gather4 copies of four rows each into a buffer of
+// kOwnSlots rows, so the buffer must hold whole copies
+static_assert(kOwnSlots % 4 == 0 && kOwnSlots <= 8, "kOwnSlots: a multiple of 4, at most 8");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -247,7 +250,7 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
 }
 
 template <int D, typename Ts, int MODEL>
-__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 320)
+__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 352)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
                       const __grid_constant__ CUtensorMap mmap)
@@ -566,8 +569,9 @@ int bulk_warps()
 {
     const int w = kBulkSmemBudget / BulkLayout<D, Ts>::BYTES;
     // the kernel's launch bound: 16 warps where the registers allow (BF16 rows
-    // halve the staging buffers, so d = 128 BF16 fits 16 warps per SM)
-    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 320) / 32;
+    // halve the staging buffers, so d = 128 BF16 fits 16 warps per SM), else
+    // 11 (FP32 rows at d = 128: 18.5 KB of staging per warp)
+    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 352) / 32;
     return w > cap ? cap : w;
 }
 
