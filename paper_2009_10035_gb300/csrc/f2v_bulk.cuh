@@ -250,7 +250,7 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
 }
 
 template <int D, typename Ts, int MODEL>
-__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 352)
+__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 384)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
                       const __grid_constant__ CUtensorMap mmap)
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
     }
 }
 
-constexpr int kBulkSmemBudget = 220 * 1024;
+constexpr int kBulkSmemBudget = 227 * 1024;   // the most shared memory one block may take
 
 template <int D, typename Ts>
 int bulk_warps()
@@ -570,8 +570,8 @@ int bulk_warps()
     const int w = kBulkSmemBudget / BulkLayout<D, Ts>::BYTES;
     // the kernel's launch bound: 16 warps where the registers allow (BF16 rows
     // halve the staging buffers, so d = 128 BF16 fits 16 warps per SM), else
-    // 11 (FP32 rows at d = 128: 18.5 KB of staging per warp)
-    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 352) / 32;
+    // 12 (FP32 rows at d = 128: 18.5 KB of staging per warp, 222 KB per block)
+    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 384) / 32;
     return w > cap ? cap : w;
 }
 
