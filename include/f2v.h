@@ -215,7 +215,10 @@ f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
                         const int32_t *neg_pairs, int64_t nneg, double *auc);
 
 /* Negative samples the device draws in epoch `epoch`: out[u*s + k] for all
-   u < n, k < s (count must equal n*s).  For checking; synchronous. */
+   u < n, k < s (count must equal n*s).  With F2V_FLAG_SHARED_SAMPLES row u
+   is the set of u's minibatch in that epoch (under F2V_FLAG_RANDOM_PARTITION,
+   the minibatch of u's position in the epoch's order).  For checking;
+   synchronous. */
 f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count);
 
 /*
