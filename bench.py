@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
+    ap.add_argument("--batched-dims", default="2,16,64",
+                    help="batched: row sizes given to the graphs round-robin")
     ap.add_argument("--no-tune", action="store_true", help="batched: default tiling, no autotune")
     return ap.parse_args()
 
@@ -447,10 +449,11 @@ BATCH_EPOCHS = 50
 
 def batched_config(gb, args, tiling=None):
     return {
-        "workload": f"force2vec-batched {gb.num_graphs} SBM graphs d{{2,16,64}} s5 b128",
+        "workload": f"force2vec-batched {gb.num_graphs} SBM graphs d{{{args.batched_dims}}} s5 b128",
         "graphs": gb.num_graphs, "n_total": int(gb.n.sum()), "nnz_total": int(gb.nnz),
         "graph": "SBM, n log-uniform [50, 20000], 2-16 equal blocks, p_in 0.05, p_out 0.002",
-        "d": "round-robin 2, 16, 64 (FP32)", "s": 5, "minibatch": 128,
+        "d": f"round-robin {args.batched_dims.replace(',', ', ')} (FP32)", "s": 5,
+        "minibatch": 128,
         "force_model": args.model, "lr": f"0.02 linearly decayed over {BATCH_EPOCHS} epochs",
         "step": "one epoch of every graph (one CUDA-graph replay)",
         "l2": "inputs larger than L2 (CSR 5.5 GB, Z 2 x 1.5 GB; L2 129 MB)",
@@ -483,7 +486,8 @@ def run_batched(args, world, rank, local):
 
     torch.cuda.set_device(local)
     model = MODEL_IDS[args.model]
-    gb = graphs.sbm_batch(args.graphs, seed=1 + rank)
+    dims = tuple(int(x) for x in args.batched_dims.split(","))
+    gb = graphs.sbm_batch(args.graphs, seed=1 + rank, dims=dims)
     s, b, lr = 5, 128, 0.02
     bt = f2v.Batch.from_graphs(gb, model=model, s=s, lr=lr, minibatch=b)
     stream = torch.cuda.ExternalStream(bt.stream)
