@@ -253,6 +253,19 @@ f2v_status f2v_eval_link_lr(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos
 f2v_status f2v_eval_kmeans(f2v_ctx *ctx, int32_t k, const int32_t *init, int32_t iters,
                            int32_t *labels, double *modularity, int32_t *rounds);
 
+/*
+ * A test of the device's bounded waits, which end every wait of the force
+ * kernels (rows of earlier minibatches, completion counters, TMA
+ * mbarriers).  One warp waits, with the same primitives and error codes,
+ * on: kind 0 a flag it has set itself (returns F2V_OK); kind 1 a row flag
+ * nothing sets; kind 2 a completion counter nothing increments; kind 3 an
+ * mbarrier nothing arrives on.  Kinds 1-3 run out after about a second and
+ * return F2V_ETIMEOUT, which, as after any timed-out epoch, leaves the
+ * context failed (F2V_ESTATE from then on); the device itself stays usable.
+ * Synchronous.
+ */
+f2v_status f2v_debug_wait(f2v_ctx *ctx, int32_t kind);
+
 /* Walks the device draws in epoch `epoch` (contexts made by f2v_create_rw):
    out[u*walk_length + i] is the vertex step i of u's walk reaches, or -1
    where the step exerts no force (u has no neighbours, the walk has

@@ -1495,6 +1495,21 @@ f2v_status f2v_eval_kmeans(f2v_ctx *ctx, int32_t k, const int32_t *init, int32_t
     return F2V_OK;
 }
 
+f2v_status f2v_debug_wait(f2v_ctx *ctx, int32_t kind)
+{
+    F2V_CHECK_CTX(ctx);
+    if (kind < 0 || kind > 3) return fail(ctx, F2V_EINVAL, "kind = %d, must be in [0, 3]", kind);
+    DeviceGuard g(ctx->device);
+    int32_t *cells = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&cells, 2 * sizeof(int32_t), ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, F2V_ENOMEM, "debug_wait: %s", cudaGetErrorString(e));
+    F2V_CUDA(ctx, cudaMemsetAsync(cells, 0, 2 * sizeof(int32_t), ctx->stream));
+    F2V_CUDA(ctx, launch_wait_probe(cells, kind, ctx->err_word, ctx->stream));
+    ctx->launches++;
+    F2V_CUDA(ctx, cudaFreeAsync(cells, ctx->stream));
+    return check_device_error(ctx);
+}
+
 f2v_status f2v_debug_walks(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t count)
 {
     F2V_CHECK_CTX(ctx);

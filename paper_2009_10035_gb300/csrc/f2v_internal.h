@@ -158,6 +158,11 @@ cudaError_t launch_mb_tables(const int64_t *apair2, int32_t n, int32_t b, int32_
 cudaError_t launch_permute_rows(const float *src, float *dst, const int32_t *perm, int64_t rows,
                                 int32_t d, bool scatter, cudaStream_t st);
 
+// One warp waiting, with the force kernels' bounded primitives, on a cell
+// (kind 1, 2) or an mbarrier (kind 3) that nothing sets; kind 0 waits on a
+// cell it has set (f2v_waits.cu).  cells: two zeroed ints.
+cudaError_t launch_wait_probe(int32_t *cells, int kind, int32_t *err, cudaStream_t st);
+
 // Downstream evaluations of Sec. IV (f2v_downstream.cu), FP64.
 size_t lr_smem_bytes(int32_t d);
 cudaError_t launch_lr_newton(const float *z, int32_t d, const int32_t *pos, int64_t npos,

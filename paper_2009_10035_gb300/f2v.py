@@ -95,6 +95,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
             "f2v_debug_samples": ([vp, i32, vp, sz], st),
             "f2v_debug_walks": ([vp, i32, vp, sz], st),
+            "f2v_debug_wait": ([vp, i32], st),
             "f2v_eval_link_lr": ([vp, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_double),
                                   vp], st),
             "f2v_eval_kmeans": ([vp, i32, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
@@ -317,6 +318,11 @@ class Context:
         self._check(self._lib.f2v_eval_kmeans(self._h, init.size, _ptr(init), int(iters),
                                               _ptr(labels), ctypes.byref(q), ctypes.byref(r)))
         return q.value, labels, r.value
+
+    def debug_wait(self, kind: int):
+        """Runs the bounded-wait test of f2v_debug_wait (raises F2VError
+        with F2V_ETIMEOUT for kinds 1-3)."""
+        self._check(self._lib.f2v_debug_wait(self._h, int(kind)))
 
     def debug_walks(self, epoch: int) -> np.ndarray:
         """n x walk_length: the vertex each walk step reaches, -1 where the

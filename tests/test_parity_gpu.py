@@ -803,3 +803,29 @@ def test_evaluations_reject_bad_arguments():
             ctx.eval_kmeans([0, 100])
         with pytest.raises(f2v.F2VError):
             ctx.eval_link_lr([[0, 1]], [[0, 2]], [1, 1])       # no test pair
+
+
+# ---------------------------------------------------------------- bounded waits
+
+def test_bounded_waits_run_out_and_report():
+    """A wait on a flag, a counter or an mbarrier that nothing sets runs out
+    after about a second and comes back as F2V_ETIMEOUT (the context is then
+    failed, as after a timed-out epoch); the device stays usable: a new
+    context trains an epoch that matches the oracle."""
+    import time
+    g = graphs.config1_graph()
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, s=5, minibatch=256, seed=1) as ctx:
+        ctx.debug_wait(0)                         # a flag that is set: no time-out
+        ctx.epoch()
+        ctx.synchronize()
+    for kind in (1, 2, 3):
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, s=5, minibatch=256, seed=1) as ctx:
+            t0 = time.perf_counter()
+            with pytest.raises(f2v.F2VError) as ei:
+                ctx.debug_wait(kind)
+            assert ei.value.status == f2v.ETIMEOUT
+            assert 0.2 < time.perf_counter() - t0 < 30.0
+            with pytest.raises(f2v.F2VError) as ei:
+                ctx.epoch()
+            assert ei.value.status == f2v.ESTATE
+    check_parity(g, 32, f2v.TDIST, 5, 256)
