@@ -115,6 +115,17 @@ cudaError_t eval_auc_device(const float *zf, const __nv_bfloat16 *zb, int d, int
                             cudaStream_t st, double *auc, std::string *err);
 }
 
+// One epoch's random partition: its order, the graph relabelled into it and
+// the chunk tables (two sets: the current epoch's, and the next one's, which
+// the side stream builds while the current epoch runs).
+struct PartSet {
+    int32_t *perm = nullptr, *rank = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
+    int64_t *apair = nullptr;
+    int32_t *mb_C = nullptr, *items = nullptr;
+    int64_t *mb_base = nullptr, *mb_p0 = nullptr;
+    int epoch = -1;                        // epoch whose order the set holds
+};
+
 struct f2v_ctx {
     int device = 0;
     int n = 0, d = 0, ld = 0, s = 0, b = 0;
@@ -157,7 +168,7 @@ struct f2v_ctx {
     // scattered back into z[cur] when the epoch ends.
     void *z[3] = {nullptr, nullptr, nullptr};   // float or bf16 rows
     int32_t *perm = nullptr, *rank = nullptr;  // the current epoch's order and its inverse
-    int perm_epoch = -1;                   // epoch whose order perm holds
+    PartSet part[2];                       // random partition: epoch e uses part[e & 1]
     PartitionScratch pw{};
     int64_t *d_mb_p0 = nullptr;            // M + 1 (random partition)
     float *master = nullptr;
@@ -194,6 +205,7 @@ struct f2v_ctx {
 
     bool failed = false;
     std::string err;
+    std::vector<void *> owned;             // every device allocation, freed once by release()
 };
 
 namespace {
@@ -241,6 +253,7 @@ f2v_status alloc(f2v_ctx *c, void **p, size_t bytes)
         return fail(c, F2V_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
     }
     c->device_bytes += bytes;
+    c->owned.push_back(*p);
     return F2V_OK;
 }
 
@@ -249,26 +262,15 @@ void release(f2v_ctx *c)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
-    void *bufs[] = {c->err_word, c->row_ptr0, c->col_idx0, c->item_u0, c->counter, c->apair0,
-                    c->z[0], c->master, c->perm, c->rank, c->pw.keys, c->pw.keys2, c->pw.vals,
-                    c->pw.deg, c->pw.cnt, c->pw.nch, c->pw.temp, c->d_mb_p0};
-    for (void *p : bufs)
-        if (p) cudaFree(p);
-    if (c->row_ptr != c->row_ptr0 && c->row_ptr) cudaFree(c->row_ptr);
-    if (c->col_idx != c->col_idx0 && c->col_idx) cudaFree(c->col_idx);
-    if (c->apair != c->apair0 && c->apair) cudaFree(c->apair);
     if (c->xstream) cudaStreamSynchronize(c->xstream);
-    void *bulk_bufs[] = {c->d_mb_item_base, c->d_mb_C, c->row_flag, c->mb_done,
-                         c->partner_buf[0], c->partner_buf[1]};
-    for (void *p : bulk_bufs)
-        if (p) cudaFree(p);
+    // the pointer fields are views; the allocations are in `owned`
+    for (auto it = c->owned.rbegin(); it != c->owned.rend(); ++it) cudaFree(*it);
+    c->owned.clear();
     for (int i = 0; i < 2; ++i) {
         if (c->ev_xdone[i]) cudaEventDestroy(c->ev_xdone[i]);
         if (c->ev_xfree[i]) cudaEventDestroy(c->ev_xfree[i]);
     }
     if (c->xstream) cudaStreamDestroy(c->xstream);
-    if (c->slots) cudaFree(c->slots);
-    if (c->unit_cnt) cudaFree(c->unit_cnt);
     for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
     for (cudaEvent_t e : c->ev_pending) cudaEventDestroy(e);
     if (prev >= 0) cudaSetDevice(prev);
@@ -561,16 +563,17 @@ bool uses_partner_list(const f2v_ctx *c)
 // The partner list of `epoch` for the graph the kernels walk (given = true:
 // for the graph as given, in id order).
 cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st,
-                                bool given = false)
+                                bool given = false, const PartSet *ps = nullptr)
 {
     c->launches++;
     const int32_t shared_b = c->shared ? c->b : 0;
     const bool relabelled = c->partition && !given;
-    const int32_t *rp = given ? c->row_ptr0 : c->row_ptr;
-    const int32_t *ci = given ? c->col_idx0 : c->col_idx;
-    const int64_t *ap = given ? c->apair0 : c->apair;
-    const int32_t *perm = relabelled ? c->perm : nullptr;
-    const int32_t *rank = relabelled ? c->rank : nullptr;
+    // a random partition's set: ps if given, else the current epoch's
+    const int32_t *rp = given ? c->row_ptr0 : (ps ? ps->row_ptr : c->row_ptr);
+    const int32_t *ci = given ? c->col_idx0 : (ps ? ps->col_idx : c->col_idx);
+    const int64_t *ap = given ? c->apair0 : (ps ? ps->apair : c->apair);
+    const int32_t *perm = relabelled ? (ps ? ps->perm : c->perm) : nullptr;
+    const int32_t *rank = relabelled ? (ps ? ps->rank : c->rank) : nullptr;
     if (c->walk > 0)
         return launch_expand_walks(rp, ci, ap, c->n, c->s, c->walk, shared_b, perm, rank,
                                    (uint32_t)epoch, (uint32_t)c->seed, (uint32_t)(c->seed >> 32),
@@ -662,37 +665,69 @@ void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochA
 // current epoch: one persistent launch for the staged kernel, one launch
 // per minibatch for the register kernel.  Each launch is bracketed by timing
 // events when timing is on.
-// Random partition: at the start of epoch e, the order of e (once per
-// epoch), the graph relabelled into it with its pair prefix and chunk tables,
-// and Z gathered into it (every time the epoch starts, since Z may have been
-// set or synchronised since).
+// Random partition.  build_partition writes epoch e's order, the graph
+// relabelled into it and its chunk tables into set ps, on stream st (the
+// main stream, or the side stream one epoch ahead); it uses the scratch c->pw,
+// so two builds never overlap.
+cudaError_t build_partition(f2v_ctx *c, int e, PartSet &ps, cudaStream_t st)
+{
+    const int M = num_minibatches(c);
+    cudaError_t err = launch_partition(c->n, (uint32_t)e, (uint32_t)c->seed,
+                                       (uint32_t)(c->seed >> 32), c->pw, ps.perm, ps.rank, st);
+    if (err == cudaSuccess)
+        err = launch_relabel(c->row_ptr0, c->col_idx0, ps.perm, ps.rank, c->n, c->s, c->walk,
+                             c->pw, ps.row_ptr, ps.col_idx, ps.apair, st);
+    const int64_t W = c->bulk ? (int64_t)c->bulk_sms * c->bulk_warps : 0;
+    if (err == cudaSuccess)
+        err = launch_mb_tables(ps.apair, c->n, c->b, M, W, c->C, c->pw, ps.mb_C, ps.mb_base,
+                               ps.items, ps.mb_p0, st);
+    c->launches += 9;
+    ps.epoch = e;
+    return err;
+}
+
+// The kernels of the current epoch read set ps.
+void use_partition(f2v_ctx *c, const PartSet &ps)
+{
+    c->perm = ps.perm;
+    c->rank = ps.rank;
+    c->row_ptr = ps.row_ptr;
+    c->col_idx = ps.col_idx;
+    c->apair = ps.apair;
+    c->item_u0 = ps.items;
+    c->d_mb_C = ps.mb_C;
+    c->d_mb_item_base = ps.mb_base;
+    c->d_mb_p0 = ps.mb_p0;
+}
+
+// At the start of epoch e: its set (built ahead on the side stream, else
+// now), the register kernel's host copy of the tables, and Z gathered into
+// the order (every time the epoch starts, since Z may have been set or
+// synchronised since).
 f2v_status prepare_partition(f2v_ctx *c, int e)
 {
     const int M = num_minibatches(c);
-    if (c->perm_epoch != e) {
-        F2V_CUDA(c, launch_partition(c->n, (uint32_t)e, (uint32_t)c->seed,
-                                     (uint32_t)(c->seed >> 32), c->pw, c->perm, c->rank,
-                                     c->stream));
-        F2V_CUDA(c, launch_relabel(c->row_ptr0, c->col_idx0, c->perm, c->rank, c->n, c->s,
-                                   c->walk, c->pw, c->row_ptr, c->col_idx, c->apair, c->stream));
-        const int64_t W = c->bulk ? (int64_t)c->bulk_sms * c->bulk_warps : 0;
-        F2V_CUDA(c, launch_mb_tables(c->apair, c->n, c->b, M, W, c->C, c->pw, c->d_mb_C,
-                                     c->d_mb_item_base, c->item_u0, c->d_mb_p0, c->stream));
-        c->launches += 9;
-        if (!c->bulk) {
-            // the register kernel takes each minibatch's tables from the host
-            F2V_CUDA(c, cudaMemcpyAsync(c->mb_C.data(), c->d_mb_C, sizeof(int32_t) * M,
-                                        cudaMemcpyDeviceToHost, c->stream));
-            F2V_CUDA(c, cudaMemcpyAsync(c->mb_item_base.data(), c->d_mb_item_base,
-                                        sizeof(int64_t) * (M + 1), cudaMemcpyDeviceToHost,
-                                        c->stream));
-            F2V_CUDA(c, cudaMemcpyAsync(c->mb_p0.data(), c->d_mb_p0, sizeof(int64_t) * (M + 1),
-                                        cudaMemcpyDeviceToHost, c->stream));
-            F2V_CUDA(c, cudaStreamSynchronize(c->stream));
-        }
-        // partner lists belong to one order
-        c->partner_epoch[0] = c->partner_epoch[1] = -1;
-        c->perm_epoch = e;
+    const int slot = e & 1;
+    PartSet &ps = c->part[slot];
+    if (ps.epoch != e) {
+        // the side stream may still be building the other set with the scratch
+        if (c->xstream) F2V_CUDA(c, cudaStreamSynchronize(c->xstream));
+        F2V_CUDA(c, build_partition(c, e, ps, c->stream));
+        c->partner_epoch[slot] = -1;      // its partner list belongs to another order
+    } else {
+        F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
+    }
+    use_partition(c, ps);
+    if (!c->bulk) {
+        // the register kernel takes each minibatch's tables from the host
+        F2V_CUDA(c, cudaMemcpyAsync(c->mb_C.data(), c->d_mb_C, sizeof(int32_t) * M,
+                                    cudaMemcpyDeviceToHost, c->stream));
+        F2V_CUDA(c, cudaMemcpyAsync(c->mb_item_base.data(), c->d_mb_item_base,
+                                    sizeof(int64_t) * (M + 1), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        F2V_CUDA(c, cudaMemcpyAsync(c->mb_p0.data(), c->d_mb_p0, sizeof(int64_t) * (M + 1),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        F2V_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     F2V_CUDA(c, launch_permute_rows((const float *)c->z[c->cur], (float *)c->z[c->cur ^ 1],
                                     c->perm, c->n, c->ld, false, c->stream));
@@ -723,10 +758,11 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
         F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
     }
     // the other buffer's last reader (epoch e - 1) is done once the work
-    // enqueued so far is: the next epoch's list may overwrite it from here
-    // (not with a random partition: the next epoch's list needs its order)
-    const bool prefetch = listed && !c->partition && k_end == num_minibatches(c) &&
-                          c->partner_epoch[slot ^ 1] != e + 1;
+    // enqueued so far is: the next epoch's list (with a random partition, the
+    // next epoch's order, relabelled graph and tables too) may overwrite it
+    const bool prefetch =
+        listed && k_end == num_minibatches(c) &&
+        (c->partition ? c->part[slot ^ 1].epoch != e + 1 : c->partner_epoch[slot ^ 1] != e + 1);
     if (prefetch) F2V_CUDA(c, cudaEventRecord(c->ev_xfree[slot ^ 1], c->stream));
     if (c->bulk)
         F2V_CUDA(c, cudaMemsetAsync(c->mb_done + k_begin, 0,
@@ -782,10 +818,16 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     }
     if (prefetch) {
         // the next epoch's partner list, on the side stream, overlapping this
-        // epoch's force launch (it only reads the graph and the epoch number)
+        // epoch's force launch (it only reads the graph and the epoch number;
+        // with a random partition, the order it builds first)
         const int ns = slot ^ 1;
         F2V_CUDA(c, cudaStreamWaitEvent(c->xstream, c->ev_xfree[ns], 0));
-        cudaError_t ee = launch_partner_list(c, e + 1, c->partner_buf[ns], c->xstream);
+        const PartSet *nps = nullptr;
+        if (c->partition) {
+            F2V_CUDA(c, build_partition(c, e + 1, c->part[ns], c->xstream));
+            nps = &c->part[ns];
+        }
+        cudaError_t ee = launch_partner_list(c, e + 1, c->partner_buf[ns], c->xstream, false, nps);
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
         F2V_CUDA(c, cudaEventRecord(c->ev_xdone[ns], c->xstream));
@@ -952,27 +994,46 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
         c->apair = c->apair0;
     }
     if (st == F2V_OK && c->partition) {
-        // the relabelled graph, the epoch's order and the scratch that builds them
+        // two sets of the epoch's order, relabelled graph and tables (the
+        // current epoch's and the next one's), and the scratch that builds them
         const size_t M = c->mb_C.size();
-        st = alloc(c, (void **)&c->row_ptr, sizeof(int32_t) * ((size_t)n + 1));
-        if (st == F2V_OK) st = alloc(c, (void **)&c->col_idx, sizeof(int32_t) * (size_t)c->nnz);
-        if (st == F2V_OK) st = alloc(c, (void **)&c->apair, sizeof(int64_t) * ((size_t)n + 1));
-        if (st == F2V_OK) st = alloc(c, (void **)&c->perm, sizeof(int32_t) * (size_t)n);
-        if (st == F2V_OK) st = alloc(c, (void **)&c->rank, sizeof(int32_t) * (size_t)n);
+        // chunk tables of any order: at most one chunk per 32 pairs plus one per minibatch
+        const size_t worst = (size_t)(c->h_apair[(size_t)n] / 32) + M + 1;
+        if (items.size() < worst) items.resize(worst, 0);
+        for (int i = 0; i < 2 && st == F2V_OK; ++i) {
+            PartSet &ps = c->part[i];
+            st = alloc(c, (void **)&ps.perm, sizeof(int32_t) * (size_t)n);
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.rank, sizeof(int32_t) * (size_t)n);
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.row_ptr, sizeof(int32_t) * ((size_t)n + 1));
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.col_idx, sizeof(int32_t) * (size_t)c->nnz);
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.apair, sizeof(int64_t) * ((size_t)n + 1));
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.mb_C, sizeof(int32_t) * M);
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.mb_base, sizeof(int64_t) * (M + 1));
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.items, sizeof(int32_t) * items.size());
+            if (st == F2V_OK) st = alloc(c, (void **)&ps.mb_p0, sizeof(int64_t) * (M + 1));
+        }
+        if (st == F2V_OK) {   // views of the set of epoch 0
+            c->row_ptr = c->part[0].row_ptr;
+            c->col_idx = c->part[0].col_idx;
+            c->apair = c->part[0].apair;
+            c->perm = c->part[0].perm;
+            c->rank = c->part[0].rank;
+            c->item_u0 = c->part[0].items;
+            c->d_mb_C = c->part[0].mb_C;
+            c->d_mb_item_base = c->part[0].mb_base;
+            c->d_mb_p0 = c->part[0].mb_p0;
+        }
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.keys, sizeof(uint32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.keys2, sizeof(uint32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.vals, sizeof(int32_t) * (size_t)n);
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.deg, sizeof(int32_t) * ((size_t)n + 1));
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.cnt, sizeof(int64_t) * ((size_t)n + 1));
         if (st == F2V_OK) st = alloc(c, (void **)&c->pw.nch, sizeof(int64_t) * (M + 1));
-        if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_p0, sizeof(int64_t) * (M + 1));
         c->pw.temp_bytes = std::max<size_t>(partition_temp_bytes(n, (int32_t)M), 16);
         if (st == F2V_OK) st = alloc(c, &c->pw.temp, c->pw.temp_bytes);
-        // chunk tables of any order: at most one chunk per 32 pairs plus one per minibatch
-        const size_t worst = (size_t)(c->h_apair[(size_t)n] / 32) + M + 1;
-        if (items.size() < worst) items.resize(worst, 0);
     }
-    if (st == F2V_OK) st = alloc(c, (void **)&c->item_u0, sizeof(int32_t) * items.size());
+    if (st == F2V_OK && !c->partition)
+        st = alloc(c, (void **)&c->item_u0, sizeof(int32_t) * items.size());
     if (st == F2V_OK) st = alloc(c, (void **)&c->counter, sizeof(int32_t) * (size_t)n);
     // Z buffers in one allocation: one TMA map then covers all of them
     const int nz = c->partition ? 3 : 2;
@@ -1005,7 +1066,7 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
                             c->stream) != cudaSuccess)
             st = fail(c, F2V_ECUDA, "memset of combine counters failed");
     }
-    if (st == F2V_OK && (c->bulk || c->partition)) {
+    if (st == F2V_OK && c->bulk && !c->partition) {
         const size_t M = c->mb_C.size();
         st = alloc(c, (void **)&c->d_mb_item_base, sizeof(int64_t) * (M + 1));
         if (st == F2V_OK) st = alloc(c, (void **)&c->d_mb_C, sizeof(int32_t) * M);
@@ -1329,6 +1390,8 @@ f2v_status f2v_debug_samples(f2v_ctx *ctx, int32_t epoch, int32_t *out, size_t c
     // position in that epoch's order
     int32_t *tperm = nullptr, *trank = nullptr;
     if (ctx->partition && ctx->shared) {
+        // (the side stream may be building the next order with the scratch)
+        if (ctx->xstream) F2V_CUDA(ctx, cudaStreamSynchronize(ctx->xstream));
         e = cudaMallocAsync((void **)&tperm, sizeof(int32_t) * (size_t)ctx->n, ctx->stream);
         if (e == cudaSuccess)
             e = cudaMallocAsync((void **)&trank, sizeof(int32_t) * (size_t)ctx->n, ctx->stream);
