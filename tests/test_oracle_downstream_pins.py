@@ -70,3 +70,21 @@ def test_modularity_closed_forms():
     ci = np.array([1, 2, 0, 2, 0, 1, 4, 5, 3, 5, 3, 4])
     assert ds.modularity(rp, ci, [0, 0, 0, 1, 1, 1]) == pytest.approx(0.5, abs=1e-15)
     assert ds.modularity(rp, ci, [0] * 6) == pytest.approx(0.0, abs=1e-15)
+
+
+def test_kmeans_tie_goes_to_the_lowest_index():
+    # 1-D points 0, 2, 1; centres start at 0 and 2; the point at 1 is as far
+    # from both and joins centre 0, which moves to 0.5 and keeps it:
+    # labels (0, 1, 0).  (Ties to the highest index would end at (0, 1, 1).)
+    labels, C, _ = ds.kmeans(np.array([[0.0], [2.0], [1.0]]), [0, 1], iters=10)
+    assert labels.tolist() == [0, 1, 0]
+    np.testing.assert_allclose(C[:, 0], [0.5, 2.0])
+
+
+def test_kmeans_empty_cluster_keeps_its_centre():
+    # points 5, 5, 20; both centres start at 5: every point ties and joins
+    # centre 0 (mean 10) while cluster 1 is empty and stays at 5; then the
+    # two 5s move to centre 1: labels (1, 1, 0), centres (20, 5).
+    labels, C, _ = ds.kmeans(np.array([[5.0], [5.0], [20.0]]), [0, 1], iters=10)
+    assert labels.tolist() == [1, 1, 0]
+    np.testing.assert_allclose(C[:, 0], [20.0, 5.0])

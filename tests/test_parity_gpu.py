@@ -829,3 +829,18 @@ def test_bounded_waits_run_out_and_report():
                 ctx.epoch()
             assert ei.value.status == f2v.ESTATE
     check_parity(g, 32, f2v.TDIST, 5, 256)
+
+
+def test_kmeans_edge_rules_on_the_device():
+    """The tie and empty-cluster rules of the oracle's pins, on the device:
+    a point as far from two centres joins the lower one; a cluster that
+    empties keeps its centre."""
+    rp = np.zeros(4, np.int32)                   # three isolated vertices
+    ci = np.zeros(0, np.int32)
+    with f2v.Context(rp, ci, 3, 1, s=1, minibatch=3, seed=1) as ctx:
+        ctx.set_embedding(np.array([[0.0], [2.0], [1.0]], np.float32))
+        _, labels, _ = ctx.eval_kmeans([0, 1], iters=10)
+        assert labels.tolist() == [0, 1, 0]
+        ctx.set_embedding(np.array([[5.0], [5.0], [20.0]], np.float32))
+        _, labels, _ = ctx.eval_kmeans([0, 1], iters=10)
+        assert labels.tolist() == [1, 1, 0]
