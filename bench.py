@@ -63,9 +63,9 @@ def parse():
     ap.add_argument("--walk", type=int, default=0,
                     help="rForce2Vec walk length (0: 1-hop neighbourhoods)")
     ap.add_argument("--shared-samples", action="store_true",
-                    help="one negative-sample set per minibatch (Algorithm 1 line 6)")
+                    help="one negative-sample set per minibatch (the sampling step of Algorithm 1)")
     ap.add_argument("--random-partition", action="store_true",
-                    help="a new random partition into minibatches every epoch (Algorithm 1 line 3)")
+                    help="a new random partition into minibatches every epoch (the partition step of Algorithm 1)")
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
@@ -84,11 +84,39 @@ def parse():
     return ap.parse_args()
 
 
+def code_only(text: str) -> str:
+    """C/C++/CUDA source with its comments removed and each run of white
+    space made one blank, string and character literals kept as written."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_hash() -> str:
+    """Hash of the force kernel's code (comments and layout ignored): the
+    stored DRAM traffic belongs to the kernel with this hash."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
+            h.update(b"\0")
     return h.hexdigest()[:16]
 
 
@@ -114,9 +142,9 @@ def workload_config(g, args, d=128, s=5, b=4096):
         "force_model": args.model, "lr": "0.02 linearly decayed",
         "neighbourhood": (f"random walks of {args.walk} steps (Algorithm 3)" if args.walk
                           else "1-hop neighbours (Algorithm 2)"),
-        "negative_samples": ("one set of s per minibatch (Algorithm 1 line 6)"
+        "negative_samples": ("one set of s per minibatch (the sampling step of Algorithm 1)"
                              if args.shared_samples else "s per vertex"),
-        "minibatches": ("a new random partition every epoch (Algorithm 1 line 3)"
+        "minibatches": ("a new random partition every epoch (the partition step of Algorithm 1)"
                         if args.random_partition else "id ranges [k b, (k+1) b)"),
         "step": "one epoch (all minibatches)",
         "l2": "inputs larger than L2 (Z 2 x 512 MB FP32 double buffer, CSR 120 MB; L2 129 MB)",

@@ -94,16 +94,18 @@ typedef enum { F2V_LR_CONSTANT = 0, F2V_LR_LINEAR = 1 } f2v_schedule;
 #define F2V_FLAG_CHECK_SYMMETRY 0x1u   /* reject a CSR that is not symmetric */
 #define F2V_FLAG_NO_STAGING 0x2u       /* use the register-gather kernel even where
                                           the shared-memory staged one exists */
-#define F2V_FLAG_SHARED_SAMPLES 0x4u   /* the literal Algorithm 1 line 6: one set S_b
-                                          of s negative samples per minibatch, used
+#define F2V_FLAG_SHARED_SAMPLES 0x4u   /* Algorithm 1's sampling step read
+                                          literally: one set S_b of s negative
+                                          samples per minibatch, used
                                           by every vertex of it (sample j of
                                           minibatch k in epoch e = Philox(key = seed,
                                           ctr = (k, e, j, 2)).x0 mod n; a sample equal
                                           to u adds no force).  Without it each vertex
                                           u draws its own s samples, ctr = (u, e, j, 0)
                                           (the O(nsd) cost of Sec. III-C). */
-#define F2V_FLAG_RANDOM_PARTITION 0x8u /* the literal Algorithm 1 line 3: a new random
-                                          partition of V every epoch.  Epoch e orders
+#define F2V_FLAG_RANDOM_PARTITION 0x8u /* Algorithm 1's partition step read
+                                          literally: a new random partition of V
+                                          every epoch.  Epoch e orders
                                           the vertices by Philox(key = seed, ctr =
                                           (v, e, 0, 3)).x0, ties by id; minibatch k is
                                           positions [k b, (k+1) b) of that order.

@@ -15,8 +15,8 @@ Every function cites the passage it follows:
                   generator both sides implement from its published definition
   init_embedding  Sec. III-C "Initialization": random Z, uniform [-0.5, 0.5)
   samples         negative samples, s per vertex (Sec. III-C complexity text)
-  samples_shared  the literal Alg. 1 line 6: one set S_b per minibatch
-  partition       the literal Alg. 1 line 3: a random partition per epoch
+  samples_shared  Alg. 1's sampling step read literally: one S_b per minibatch
+  partition       Alg. 1's partition step read literally: new each epoch
   grad_minibatch  Algorithm 2, per-pair terms Eq. 5/6 (sigmoid), Eq. 8/9 (t),
                   Table "diffmodels" (FR, LinLog, ForceAtlas)
   walk            Algorithm 3 (GenWalk), the rForce2Vec neighbourhood
@@ -195,7 +195,7 @@ def walk(row_ptr, col_idx, u: int, epoch: int, k: int, seed: int) -> np.ndarray:
 
 
 def samples_shared(n: int, s: int, b: int, epoch: int, seed: int) -> np.ndarray:
-    """The literal Algorithm 1 line 6: row u lists the set S_b of u's
+    """Algorithm 1's sampling step read literally: row u lists the set S_b of u's
     minibatch (k = u // b), an n x s int32 array."""
     lib = _load()
     out = np.zeros((n, s), dtype=np.int32)
@@ -238,7 +238,7 @@ def grad_minibatch_abs(model, row_ptr, col_idx, Z, u_begin, u_end, s, seed, epoc
 
 
 def partition(n: int, epoch: int, seed: int) -> np.ndarray:
-    """The random partition of an epoch (Alg. 1 line 3): the vertices in
+    """The random partition of an epoch (the partition step of Alg. 1): the vertices in
     minibatch order; minibatch k is positions [k b, (k+1) b)."""
     lib = _load()
     perm = np.zeros(max(n, 1), dtype=np.int64)
@@ -276,8 +276,8 @@ def train(model, row_ptr, col_idx, Z, s, b, seed, lr, epochs, start_epoch=0,
           walk=0, shared=False, partition=False) -> np.ndarray:
     """Algorithm 1 from embedding Z (copied); returns the new FP64 embedding.
     walk > 0: rForce2Vec, N(u) from Algorithm 3 with walks of that length.
-    shared: one sample set S_b per minibatch (the literal line 6).
-    partition: a new random partition every epoch (the literal line 3)."""
+    shared: one sample set S_b per minibatch (the sampling step read literally).
+    partition: a new random partition every epoch (the partition step read literally)."""
     lib = _load()
     row_ptr, col_idx = _csr(row_ptr, col_idx)
     Z = np.array(Z, dtype=np.float64, order="C", copy=True)

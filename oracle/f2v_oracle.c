@@ -18,7 +18,7 @@
  *   orc_sample          uniform negative sample for vertex u (Sec. III-C,
  *                       negative sampling; one set of s samples per vertex as
  *                       in the complexity paragraph of Sec. III-C).
- *   orc_sample_shared   the literal form of Alg. 1 line 6: one set S_b of s
+ *   orc_sample_shared   Alg. 1's sampling step read literally: one set S_b of s
  *                       samples per minibatch, used by every vertex of it
  *                       (Sec. III-C, the paragraph after Alg. 1).
  *   attractive_grad,    per-pair gradients: sigmoid model Eq. 5 / Eq. 6,
@@ -40,11 +40,11 @@
  *     rows are then updated; the next minibatch sees those updates.
  *   - Minibatch k holds vertex ids [k*b, min((k+1)*b, n)) in id order; or,
  *     as an option, the positions [k*b, min((k+1)*b, n)) of a random
- *     permutation drawn anew each epoch (Alg. 1 line 3, "randomly without
- *     replacement"): vertices sorted by Philox(key, ctr=(v, e, 0, 3)).x0,
+ *     permutation drawn anew each epoch (the partition step of Alg. 1: random
+ *     minibatches, no vertex in two of them): vertices sorted by Philox(key, ctr=(v, e, 0, 3)).x0,
  *     ties by id (orc_partition).  Shared samples then belong to the
  *     minibatch index k.
- *   - Only z_u for u in the minibatch is updated (Algorithm 1, lines 8-9).
+ *   - Only z_u for u in the minibatch is updated (the update step of Algorithm 1).
  *   - Negative sample k of vertex u in epoch e is
  *       w = Philox(key=(seed lo, seed hi), ctr=(u, e, k, 0)).x0 mod n,
  *     with no neighbour rejection; w == u contributes nothing.
@@ -78,7 +78,7 @@
  *     Their forces grow (FR, LinLog, ForceAtlas attraction) or stay finite
  *     with distance, so like the sigmoid model they take the coordinate
  *     bound below.
- *   - Shared samples (the literal Alg. 1 line 6, an option): sample j of
+ *   - Shared samples (Alg. 1's sampling step read literally, an option): sample j of
  *     minibatch k in epoch e is Philox(key, ctr=(k, e, j, 2)).x0 mod n for
  *     every vertex of the minibatch; a sample equal to u adds no force.
  *   - Sigmoid (and FR, LinLog, ForceAtlas) models: after each update every
@@ -470,8 +470,8 @@ void orc_grad_minibatch(int model, int64_t n, int32_t d,
 /* ------------------------------------------------------------------ */
 
 /*
- * The random partition of epoch e (Alg. 1 line 3, "randomly without
- * replacement"): perm lists the vertices in increasing order of the key
+ * The random partition of epoch e (the partition step of Alg. 1: random
+ * minibatches, no vertex in two of them): perm lists the vertices in increasing order of the key
  * Philox(key, ctr=(v, e, 0, 3)).x0, ties by id; minibatch k is
  * perm[k b .. min((k+1) b, n)).
  */
@@ -534,7 +534,7 @@ int orc_train_ex(int model, int64_t n, int32_t d,
     }
     for (int32_t e = start_epoch; e < start_epoch + epochs; ++e) {
         const double eta = orc_learning_rate(lr0, schedule, total_epochs, e);
-        /* line 3: the minibatches of this epoch */
+        /* the minibatches of this epoch */
         if (partition) {
             if (orc_partition(seed, n, e, perm) != 0) {
                 free(grad);

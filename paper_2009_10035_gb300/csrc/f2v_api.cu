@@ -130,8 +130,8 @@ struct f2v_ctx {
     int device = 0;
     int n = 0, d = 0, ld = 0, s = 0, b = 0;
     int walk = 0;                          // rForce2Vec walk length (0: neighbours, Alg. 2)
-    bool shared = false;                   // one sample set S_b per minibatch (Alg. 1 line 6)
-    bool partition = false;                // a new random partition every epoch (Alg. 1 line 3)
+    bool shared = false;                   // one sample set S_b per minibatch (Alg. 1's sampling step)
+    bool partition = false;                // a new random partition every epoch (Alg. 1's partition step)
     int64_t nnz = 0;
     int64_t pairs = 0;                     // force pairs per epoch
     int model = 0;

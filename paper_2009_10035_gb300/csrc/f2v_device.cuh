@@ -36,7 +36,7 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
 // the paper's random start).
 // Negative sample k of vertex u in epoch `epoch`: its own draw
 // Philox(ctr = (u, epoch, k, 0)).x0 mod n, or, with kb >= 0 (one set S_b
-// per minibatch, the literal Alg. 1 line 6), the draw of minibatch kb,
+// per minibatch, Alg. 1's sampling step read literally), the draw of minibatch kb,
 // Philox(ctr = (kb, epoch, k, 2)).x0 mod n.
 __device__ __forceinline__ uint32_t negative_sample(int64_t u, int64_t kb, uint32_t epoch,
                                                     uint32_t k, int32_t n, uint32_t key0,

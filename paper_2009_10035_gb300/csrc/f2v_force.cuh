@@ -1,5 +1,5 @@
 // f2v_force.cuh -- the fused SDDMM + SpMM force kernel and SGD update of one
-// minibatch (Algorithm 2 followed by lines 8-9 of Algorithm 1, Eq. 10).
+// minibatch (Algorithm 2 followed by the update step of Algorithm 1, Eq. 10).
 //
 // Work decomposition.  The minibatch's force pairs (neighbours of each u in
 // CSR order, then its s negative samples) form one flat sequence; it is cut

@@ -127,7 +127,7 @@ cudaError_t launch_expand_walks(const int32_t *row_ptr, const int32_t *col_idx,
                                 uint32_t epoch, uint32_t key0, uint32_t key1, int32_t *partner,
                                 cudaStream_t st);
 
-// The random partition of an epoch (Algorithm 1 line 3), f2v_partition.cu.
+// The random partition of an epoch (the partition step of Algorithm 1), f2v_partition.cu.
 struct PartitionScratch {
     uint32_t *keys, *keys2;    // n: sort keys
     int32_t *vals;             // n: sort values (vertex ids)

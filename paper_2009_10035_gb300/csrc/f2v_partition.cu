@@ -1,5 +1,6 @@
 // f2v_partition.cu -- a new random partition of V into minibatches every
-// epoch (Algorithm 1 line 3, "randomly without replacement"), as an option.
+// epoch (the partition step of Algorithm 1: random minibatches, no vertex
+// in two of them), as an option.
 //
 // Epoch e orders the vertices by the key Philox4x32-10(key, ctr = (v, e, 0,
 // 3)).x0, ties by id (a stable radix sort of (key, v)); minibatch k is the

@@ -59,6 +59,85 @@ def header_functions() -> list[str]:
     return sorted(names)
 
 
+def signatures() -> dict:
+    """ctypes (argument types, result type) of every function of the C ABI."""
+    i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
+    vp, sz, f32, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    return {
+        "f2v_create": ([vp, vp, i32, i32, st, i32, f32, i32, u64, pp], st),
+        "f2v_create_ex": ([vp, vp, i32, i32, st, i32, f32, i32, u64, st, u32, vp, pp], st),
+        "f2v_create_rw": ([vp, vp, i32, i32, st, i32, i32, f32, i32, u64, st, u32, vp, pp],
+                          st),
+        "f2v_destroy": ([vp], None),
+        "f2v_epoch": ([vp], st),
+        "f2v_train": ([vp, i32], st),
+        "f2v_run_minibatches": ([vp, i32], st),
+        "f2v_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+        "f2v_synchronize": ([vp], st),
+        "f2v_get_embedding": ([vp, vp, sz], st),
+        "f2v_get_embedding_device": ([vp, vp, sz], st),
+        "f2v_set_embedding": ([vp, vp, sz], st),
+        "f2v_set_lr": ([vp, f32], st),
+        "f2v_set_schedule": ([vp, st, i32], st),
+        "f2v_set_epoch": ([vp, i32], st),
+        "f2v_get_epoch": ([vp, ctypes.POINTER(i32)], st),
+        "f2v_set_stream": ([vp, vp], st),
+        "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
+        "f2v_debug_samples": ([vp, i32, vp, sz], st),
+        "f2v_debug_walks": ([vp, i32, vp, sz], st),
+        "f2v_debug_wait": ([vp, i32], st),
+        "f2v_eval_link_lr": ([vp, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_double),
+                              vp], st),
+        "f2v_eval_kmeans": ([vp, i32, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(i32)], st),
+        "f2v_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+        "f2v_device_bytes": ([vp, ctypes.POINTER(sz)], st),
+        "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
+        "f2v_set_kernel_timing": ([vp, i32], st),
+        "f2v_read_kernel_timing": ([vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)], st),
+        "f2v_minibatch_noalloc": ([vp, vp, i32, i32, st, i32, f32, u64, i32, i32, i32, vp,
+                                   vp, vp], st),
+        "f2v_noalloc_last_error": ([], ctypes.c_char_p),
+        "f2v_last_error": ([vp], ctypes.c_char_p),
+        "f2v_last_error_global": ([], ctypes.c_char_p),
+        # batched form (include/f2v_batch.h)
+        "f2v_batch_create": ([i32, vp, vp, vp, vp, vp, st, i32, f32, i32, st, vp, pp], st),
+        "f2v_batch_destroy": ([vp], None),
+        "f2v_batch_epoch": ([vp], st),
+        "f2v_batch_train": ([vp, i32], st),
+        "f2v_batch_synchronize": ([vp], st),
+        "f2v_batch_run_minibatches": ([vp, i32], st),
+        "f2v_batch_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+        "f2v_batch_set_lr": ([vp, f32], st),
+        "f2v_batch_set_schedule": ([vp, st, i32], st),
+        "f2v_batch_get_epoch": ([vp, ctypes.POINTER(i32)], st),
+        "f2v_batch_get_embedding": ([vp, i32, vp, sz], st),
+        "f2v_batch_get_embeddings": ([vp, vp, sz], st),
+        "f2v_batch_set_embedding": ([vp, i32, vp, sz], st),
+        "f2v_batch_set_tiling": ([vp, vp], st),
+        "f2v_batch_get_tiling": ([vp, i32, vp], st),
+        "f2v_batch_autotune": ([vp, i32, vp, i32, ctypes.POINTER(i32)], st),
+        "f2v_batch_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+        "f2v_batch_bytes_per_epoch": ([vp, ctypes.POINTER(i64)], st),
+        "f2v_batch_device_bytes": ([vp, ctypes.POINTER(sz)], st),
+        "f2v_batch_num_graphs": ([vp, ctypes.POINTER(i32)], st),
+        "f2v_batch_launch_count": ([vp, ctypes.POINTER(i64)], st),
+        "f2v_batch_stream": ([vp, pp], st),
+        "f2v_batch_last_error": ([vp], ctypes.c_char_p),
+        # served form (include/f2v_serve.h)
+        "f2v_server_create": ([sz, i32, pp], st),
+        "f2v_server_submit": ([vp, vp, ctypes.POINTER(i64)], st),
+        "f2v_server_job": ([vp, i64, vp], st),
+        "f2v_server_wait": ([vp, i64], st),
+        "f2v_server_wait_all": ([vp], st),
+        "f2v_server_get_stats": ([vp, vp], st),
+        "f2v_server_destroy": ([vp], None),
+        "f2v_server_last_error": ([vp], ctypes.c_char_p),
+        "f2v_server_job_error": ([vp, i64], ctypes.c_char_p),
+    }
+
+
 def load_library(path: str | None = None) -> ctypes.CDLL:
     """Loads libf2v.so and declares its signatures (raises if it is missing)."""
     global _lib
@@ -70,82 +149,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
             raise RuntimeError(f"libf2v.so is not built ({p}); run "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")
         lib = ctypes.CDLL(p)
-        i32, i64, u32, u64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
-        vp, sz, f32, st = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
-        pp = ctypes.POINTER(ctypes.c_void_p)
-        sigs = {
-            "f2v_create": ([vp, vp, i32, i32, st, i32, f32, i32, u64, pp], st),
-            "f2v_create_ex": ([vp, vp, i32, i32, st, i32, f32, i32, u64, st, u32, vp, pp], st),
-            "f2v_create_rw": ([vp, vp, i32, i32, st, i32, i32, f32, i32, u64, st, u32, vp, pp],
-                              st),
-            "f2v_destroy": ([vp], None),
-            "f2v_epoch": ([vp], st),
-            "f2v_train": ([vp, i32], st),
-            "f2v_run_minibatches": ([vp, i32], st),
-            "f2v_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
-            "f2v_synchronize": ([vp], st),
-            "f2v_get_embedding": ([vp, vp, sz], st),
-            "f2v_get_embedding_device": ([vp, vp, sz], st),
-            "f2v_set_embedding": ([vp, vp, sz], st),
-            "f2v_set_lr": ([vp, f32], st),
-            "f2v_set_schedule": ([vp, st, i32], st),
-            "f2v_set_epoch": ([vp, i32], st),
-            "f2v_get_epoch": ([vp, ctypes.POINTER(i32)], st),
-            "f2v_set_stream": ([vp, vp], st),
-            "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
-            "f2v_debug_samples": ([vp, i32, vp, sz], st),
-            "f2v_debug_walks": ([vp, i32, vp, sz], st),
-            "f2v_debug_wait": ([vp, i32], st),
-            "f2v_eval_link_lr": ([vp, vp, i64, vp, i64, vp, ctypes.POINTER(ctypes.c_double),
-                                  vp], st),
-            "f2v_eval_kmeans": ([vp, i32, vp, i32, vp, ctypes.POINTER(ctypes.c_double),
-                                 ctypes.POINTER(i32)], st),
-            "f2v_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
-            "f2v_device_bytes": ([vp, ctypes.POINTER(sz)], st),
-            "f2v_launch_count": ([vp, ctypes.POINTER(i64)], st),
-            "f2v_set_kernel_timing": ([vp, i32], st),
-            "f2v_read_kernel_timing": ([vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)], st),
-            "f2v_minibatch_noalloc": ([vp, vp, i32, i32, st, i32, f32, u64, i32, i32, i32, vp,
-                                       vp, vp], st),
-            "f2v_noalloc_last_error": ([], ctypes.c_char_p),
-            "f2v_last_error": ([vp], ctypes.c_char_p),
-            "f2v_last_error_global": ([], ctypes.c_char_p),
-            # batched form (include/f2v_batch.h)
-            "f2v_batch_create": ([i32, vp, vp, vp, vp, vp, st, i32, f32, i32, st, vp, pp], st),
-            "f2v_batch_destroy": ([vp], None),
-            "f2v_batch_epoch": ([vp], st),
-            "f2v_batch_train": ([vp, i32], st),
-            "f2v_batch_synchronize": ([vp], st),
-            "f2v_batch_run_minibatches": ([vp, i32], st),
-            "f2v_batch_get_progress": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
-            "f2v_batch_set_lr": ([vp, f32], st),
-            "f2v_batch_set_schedule": ([vp, st, i32], st),
-            "f2v_batch_get_epoch": ([vp, ctypes.POINTER(i32)], st),
-            "f2v_batch_get_embedding": ([vp, i32, vp, sz], st),
-            "f2v_batch_get_embeddings": ([vp, vp, sz], st),
-            "f2v_batch_set_embedding": ([vp, i32, vp, sz], st),
-            "f2v_batch_set_tiling": ([vp, vp], st),
-            "f2v_batch_get_tiling": ([vp, i32, vp], st),
-            "f2v_batch_autotune": ([vp, i32, vp, i32, ctypes.POINTER(i32)], st),
-            "f2v_batch_pairs_per_epoch": ([vp, ctypes.POINTER(i64)], st),
-            "f2v_batch_bytes_per_epoch": ([vp, ctypes.POINTER(i64)], st),
-            "f2v_batch_device_bytes": ([vp, ctypes.POINTER(sz)], st),
-            "f2v_batch_num_graphs": ([vp, ctypes.POINTER(i32)], st),
-            "f2v_batch_launch_count": ([vp, ctypes.POINTER(i64)], st),
-            "f2v_batch_stream": ([vp, pp], st),
-            "f2v_batch_last_error": ([vp], ctypes.c_char_p),
-            # served form (include/f2v_serve.h)
-            "f2v_server_create": ([sz, i32, pp], st),
-            "f2v_server_submit": ([vp, vp, ctypes.POINTER(i64)], st),
-            "f2v_server_job": ([vp, i64, vp], st),
-            "f2v_server_wait": ([vp, i64], st),
-            "f2v_server_wait_all": ([vp], st),
-            "f2v_server_get_stats": ([vp, vp], st),
-            "f2v_server_destroy": ([vp], None),
-            "f2v_server_last_error": ([vp], ctypes.c_char_p),
-            "f2v_server_job_error": ([vp, i64], ctypes.c_char_p),
-        }
-        for name, (args, res) in sigs.items():
+        for name, (args, res) in signatures().items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = res

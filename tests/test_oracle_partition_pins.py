@@ -1,5 +1,5 @@
-"""Pins of the oracle's random-partition option: the literal Algorithm 1
-line 3, a new partition of V into minibatches every epoch.
+"""Pins of the oracle's random-partition option: Algorithm 1's partition
+step read literally, a new partition of V into minibatches every epoch.
 
 The partitioned run is tied to the contiguous one, which the other pins fix:
 one epoch over the partition of epoch e is one epoch of the contiguous

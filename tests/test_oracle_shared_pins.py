@@ -1,5 +1,6 @@
-"""Pins of the oracle's shared-sample option: the literal Algorithm 1 line 6,
-one set S_b of s negative samples per minibatch used by every vertex of it.
+"""Pins of the oracle's shared-sample option: Algorithm 1's sampling step
+read literally, one set S_b of s negative samples per minibatch used by
+every vertex of it.
 
 The shared draw is tied to facts outside its code: the injected-sample path
 of Algorithm 2 (pinned by the closed forms of test_oracle_pins.py) must give

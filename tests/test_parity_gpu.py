@@ -561,7 +561,7 @@ def test_rmat_scale20_d128_other_models(model, rmat20):
     print(f"rmat20 model={model}: worst scaled error {worst:.3e}")
 
 
-# ---------------------------------------------------------------- shared samples (Alg. 1 line 6)
+# ------------------------------------------------- shared samples (Alg. 1's sampling step)
 
 @pytest.mark.parametrize("b", [1, 100, 256])
 def test_shared_samples_bit_exact(b):
@@ -616,7 +616,7 @@ def test_rmat_scale20_d128_shared_samples(model, rmat20):
     print(f"rmat20 shared samples model={model}: worst scaled error {worst:.3e}")
 
 
-# ---------------------------------------------------------------- random partition (Alg. 1 line 3)
+# ----------------------------------------------- random partition (Alg. 1's partition step)
 
 def check_partition_steps(g, d, model, s, b, lr=0.05, seed=4, epochs=2, steps=None, flags=0,
                           walk=0, tol=TOL_STEP):
