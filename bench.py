@@ -834,7 +834,7 @@ def main():
         else:
             run_served(args, world, rank, local)
     else:
-        g = graphs.config2_graph(scale=args.scale)
+        g = graphs.rmat_holdout_graph(scale=args.scale)
         if args.impl == "reference":
             run_reference(args, g, world, rank)
         else:

@@ -246,12 +246,12 @@ def star(n_leaves: int) -> Graph:
     return from_edges(n_leaves + 1, u, v, name=f"star-{n_leaves}")
 
 
-def config1_graph(seed: int = 1) -> Graph:
+def er1000_graph(seed: int = 1) -> Graph:
     """Erdos-Renyi n=1000 with p chosen for ~10,000 undirected edges."""
     return erdos_renyi(1000, m=10000, seed=seed)
 
 
-def config2_graph(seed: int = 1, scale: int = 20, frac: float = 0.05) -> Graph:
+def rmat_holdout_graph(seed: int = 1, scale: int = 20, frac: float = 0.05) -> Graph:
     """R-MAT scale-20 (16 * 2^20 directed edges, a=.57, b=c=.19), symmetrised,
     with `frac` of the undirected edges held out."""
     return holdout(rmat(scale, 16, seed=seed), frac=frac, seed=seed + 1000)

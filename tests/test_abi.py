@@ -70,7 +70,7 @@ def test_python_binding_refuses_missing_library(tmp_path):
 
 
 def test_graph_generators_give_valid_symmetric_csr():
-    for g in (graphs.config1_graph(), graphs.rmat(10, 8, seed=3), graphs.sbm(500, 4, 0.05, 0.002),
+    for g in (graphs.er1000_graph(), graphs.rmat(10, 8, seed=3), graphs.sbm(500, 4, 0.05, 0.002),
               graphs.star(50)):
         n = g.n
         deg = g.degrees()
@@ -86,8 +86,8 @@ def test_graph_generators_give_valid_symmetric_csr():
             assert (np.diff(row) > 0).all()
 
 
-def test_config1_graph_shape():
-    g = graphs.config1_graph()
+def test_er1000_graph_shape():
+    g = graphs.er1000_graph()
     assert g.n == 1000
     assert 9000 < g.nnz // 2 < 11000
 

@@ -344,7 +344,7 @@ def test_thread_count_does_not_change_result():
 
 @pytest.mark.parametrize("model", ["tdist", "sigmoid"])
 def test_loss_decreases_over_first_epochs(model):
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     m = MODELS[model]
     Z = oracle.init_embedding(g.n, 32, 1)
     # loss over a fixed sample set so that the comparisons are like for like

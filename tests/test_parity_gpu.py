@@ -147,7 +147,7 @@ def test_negative_samples_bit_exact(n, s):
 @pytest.mark.parametrize("model", MODELS)
 def test_er_n1000_d32_one_epoch(model):
     """Erdos-Renyi n=1000, ~10,000 edges, d=32, s=5, b=256, lr=0.02."""
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     check_parity(g, 32, model, s=5, b=256, lr=0.02, seed=1)
 
 
@@ -261,7 +261,7 @@ def test_split_epoch_equals_whole_epoch():
 
 @pytest.mark.parametrize("model", MODELS)
 def test_three_epochs_linear_schedule(model):
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     got = gpu_run(g, 32, model, 5, 256, 0.02, 1, 3, schedule=f2v.LR_LINEAR, total_epochs=3)
     want = oracle_run(g, 32, model, 5, 256, 0.02, 1, 3, schedule=1, total_epochs=3)
     assert rel_err(got, want).max() <= 1e-4
@@ -276,7 +276,7 @@ def test_runs_are_bit_reproducible():
 
 @pytest.mark.parametrize("model", MODELS)
 def test_resume_is_bit_identical(model):
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     full = gpu_run(g, 32, model, 5, 256, 0.02, 7, 3)
     with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, lr=0.02,
                      minibatch=256, seed=7) as ctx:
@@ -307,7 +307,7 @@ def test_auc_matches_oracle_on_same_embedding(model):
 
 
 def test_error_status_for_bad_arguments():
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     with f2v.Context(g.row_ptr, g.col_idx, g.n, 32) as ctx:
         with pytest.raises(f2v.F2VError):
             ctx.set_embedding(np.zeros(5, np.float32))
@@ -349,7 +349,7 @@ def test_bf16_bit_reproducible_and_resumable(model):
 
 @pytest.fixture(scope="module")
 def rmat20():
-    return graphs.config2_graph()
+    return graphs.rmat_holdout_graph()
 
 
 @pytest.mark.parametrize("model", MODELS)
@@ -525,7 +525,7 @@ def test_other_models_one_epoch(model):
     cancelled; on this graph one element of 32,000 reaches 2.2e-5 relative
     to its own size, while the launches themselves all meet the scaled
     per-minibatch bound.)"""
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     got = gpu_run(g, 32, model, 5, 256, 0.01, 1, 1)
     want = oracle_run(g, 32, model, 5, 256, 0.01, 1, 1)
     assert np.isfinite(got).all()
@@ -594,7 +594,7 @@ def test_shared_samples_with_walks_and_bf16(model):
 
 @pytest.mark.parametrize("model", MODELS)
 def test_shared_samples_one_epoch(model):
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, model=model, s=5, lr=0.02, minibatch=256,
                      seed=1, flags=f2v.FLAG_SHARED_SAMPLES) as ctx:
         ctx.epoch()
@@ -675,7 +675,7 @@ def test_partition_with_walks_shared_samples_and_fr(d):
 
 @pytest.mark.parametrize("d", [32, 128])
 def test_partition_whole_epochs(d):
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     with f2v.Context(g.row_ptr, g.col_idx, g.n, d, s=5, lr=0.02, minibatch=256, seed=1,
                      flags=f2v.FLAG_RANDOM_PARTITION) as ctx:
         ctx.train(3)
@@ -813,7 +813,7 @@ def test_bounded_waits_run_out_and_report():
     failed, as after a timed-out epoch); the device stays usable: a new
     context trains an epoch that matches the oracle."""
     import time
-    g = graphs.config1_graph()
+    g = graphs.er1000_graph()
     with f2v.Context(g.row_ptr, g.col_idx, g.n, 32, s=5, minibatch=256, seed=1) as ctx:
         ctx.debug_wait(0)                         # a flag that is set: no time-out
         ctx.epoch()

@@ -37,7 +37,7 @@ def test_noalloc_minibatch_matches_context(model):
         pytest.skip("no CUDA device")
     torch.cuda.set_device(0)
     lib = f2v.load_library()
-    g = graphs.config1_graph()                 # n=1000, ~10,000 edges
+    g = graphs.er1000_graph()                 # n=1000, ~10,000 edges
     d, s, b, lr, seed = 32, 5, 256, 0.02, 1
 
     # the existing entry points: a context, one minibatch at a time
