@@ -162,6 +162,18 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _host_out(out, count: int, exact: bool = True) -> np.ndarray:
+    """Checks a caller's output buffer: writable, C-contiguous float32 with
+    `count` elements (at least `count` where exact is False)."""
+    if not isinstance(out, np.ndarray) or out.dtype != np.float32:
+        raise ValueError("output must be a float32 numpy array")
+    if not out.flags.c_contiguous or not out.flags.writeable:
+        raise ValueError("output must be C-contiguous and writable")
+    if (out.size != count) if exact else (out.size < count):
+        raise ValueError(f"output holds {out.size} floats, needs {count}")
+    return out
+
+
 def _stream_handle(stream) -> int | None:
     if stream is None:
         return None
@@ -252,7 +264,7 @@ class Context:
         return out
 
     def embedding_into_host(self, out: np.ndarray):
-        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size == self.n * self.d
+        _host_out(out, self.n * self.d)
         self._check(self._lib.f2v_get_embedding(self._h, _ptr(out), out.size))
 
     def embedding_into_device(self, dev_ptr: int):
@@ -477,7 +489,7 @@ class Batch:
 
     def embeddings_into_host(self, out: np.ndarray):
         """All graphs' Z, concatenated in graph order (row-major per graph)."""
-        assert out.dtype == np.float32 and out.flags.c_contiguous
+        _host_out(out, int(self.z_off[-1]))
         self._check(self._lib.f2v_batch_get_embeddings(self._h, _ptr(out), out.size))
 
     def set_embedding(self, g: int, z):
@@ -631,7 +643,7 @@ class Server:
             ci = np.zeros(1, np.int32)
         if out is None:
             out = np.empty((int(n), int(d)), np.float32)
-        assert out.dtype == np.float32 and out.flags.c_contiguous and out.size >= int(n) * int(d)
+        _host_out(out, int(n) * int(d), exact=False)
         spec = JobSpec(_ptr(rp).value, _ptr(ci).value, int(n), int(d), int(model), int(s),
                        float(lr), int(minibatch), int(seed) & (2**64 - 1), int(epochs),
                        int(precision), _ptr(out).value)

@@ -103,3 +103,18 @@ def test_holdout_split_is_disjoint_and_balanced():
     assert pos.isdisjoint(train) and pos | train == full
     assert neg.isdisjoint(full)
     assert all(a < b for a, b in g.test_neg)
+
+
+def test_output_buffers_are_checked_before_the_call():
+    ok = np.zeros(12, np.float32)
+    assert f2v._host_out(ok, 12) is ok
+    assert f2v._host_out(np.zeros(20, np.float32), 12, exact=False) is not None
+    ro = np.zeros(12, np.float32)
+    ro.flags.writeable = False
+    bad = [np.zeros(12, np.float64), np.zeros((4, 6), np.float32)[:, :3], ro,
+           np.zeros(11, np.float32), [0.0] * 12]
+    for out in bad:
+        with pytest.raises(ValueError):
+            f2v._host_out(out, 12)
+    with pytest.raises(ValueError):
+        f2v._host_out(np.zeros(11, np.float32), 12, exact=False)
