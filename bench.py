@@ -120,6 +120,27 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu), or the
+    machine type where neither names it."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine() or "unknown"
+
+
 def hbm_peak():
     try:
         with open(PEAKS_FILE) as f:
@@ -308,7 +329,7 @@ def run_reference(args, g, world, rank):
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(g, args),
-        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -450,7 +471,7 @@ def run_ours(args, g, world, rank, local):
     if rank == 0 and world == 1 and not args.skip_cpu:
         rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds, walk=args.walk,
                                                     shared=args.shared_samples)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"first {mbs} minibatches (b=4096) of epoch 0, {pairs} pairs, FP64, "
                          f"{el:.1f} s"}
 
@@ -584,7 +605,7 @@ def run_batched(args, world, rank, local):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         rate, pairs, ng, threads, el = batched_oracle_rate(gb, model, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": "pairs/s", "cores": threads, "cpu": cpu_model(), "kind": "oracle",
                "sample": f"one epoch of the first {ng} graphs, {pairs} pairs, FP64, {el:.1f} s"}
     if rank == 0:
         line = {

@@ -28,3 +28,8 @@ def test_kernel_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_hash() == h0
     f.write_text("__global__ void k(int *p) { p[0] = 2; }\n")
     assert bench.kernel_hash() != h0
+
+
+def test_cpu_model_names_the_host():
+    name = bench.cpu_model()
+    assert isinstance(name, str) and name.strip()
