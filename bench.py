@@ -127,14 +127,14 @@ def cpu_model() -> str:
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith("model name"):
+                if line.lower().startswith("model name") and ":" in line:
                     return line.split(":", 1)[1].strip()
-    except OSError:
+    except Exception:
         pass
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
         for line in out.splitlines():
-            if line.strip().lower().startswith("model name"):
+            if line.strip().lower().startswith("model name") and ":" in line:
                 return line.split(":", 1)[1].strip()
     except Exception:
         pass
