@@ -4,11 +4,14 @@
  * Force2Vec (Rahman, Sujon, Azad, arXiv:2009.10035) embeds the vertices of an
  * undirected graph G(V, E) with 0/1 adjacency A (Sec. II-A) into Z in R^{n x d}
  * by minibatch SGD on the negative-sampling loss of Eq. 2.  Each epoch
- * (Algorithm 1) visits the vertices in minibatches V_b of b consecutive ids;
- * for every u in V_b it sums the attractive gradient over its neighbours N(u)
- * and the repulsive gradient over s negative samples (Algorithm 2), using Z as
- * it stood when the minibatch began, and then applies z_u -= eta * grad
- * (Eq. 10).  Two force models are offered:
+ * (Algorithm 1) visits the vertices in minibatches V_b of b consecutive ids
+ * (or, with F2V_FLAG_RANDOM_PARTITION, b consecutive positions of a new
+ * random order); for every u in V_b it sums the attractive gradient over its
+ * neighbours N(u) (or, for a context made by f2v_create_rw, over the
+ * vertices of a random walk from u, Algorithm 3) and the repulsive gradient
+ * over s negative samples (Algorithm 2), using Z as it stood when the
+ * minibatch began, and then applies z_u -= eta * grad (Eq. 10).  The force
+ * models (f2v_model below):
  *   F2V_TDIST    t-distribution similarity, Eq. 7; gradients Eq. 8 / Eq. 9
  *                times the unit vector (z_u - z_x)/t of Sec. III-B.  t^2 is
  *                floored at 1e-8 in the repulsive term.
@@ -16,11 +19,16 @@
  *                after each update the coordinates of z_u are clamped to
  *                [-4, 4] (the paper is silent; unbounded, the summed
  *                gradients of high-degree vertices make the run diverge).
+ *   F2V_FR, F2V_LINLOG, F2V_FORCEATLAS  the force laws of Table "diffmodels",
+ *                with the same repulsion and clamp.
  *
  * Conventions shared by every entry point:
  *   - All functions return f2v_status and never abort.  A failure leaves a
  *     message readable through f2v_last_error (per context) or
  *     f2v_last_error_global (for f2v_create* before a context exists).
+ *   - An invalid argument (a size out of range, a NULL buffer where one is
+ *     required, a combination a form does not support) returns F2V_EINVAL
+ *     before any device work and leaves the context usable.
  *   - A CUDA error inside a context makes it sticky-failed: every later call
  *     on it returns F2V_ESTATE until f2v_destroy.
  *   - Host arrays passed in stay owned by the caller and are copied before the
