@@ -14,6 +14,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -959,8 +960,9 @@ f2v_status create_impl(const int32_t *row_ptr, const int32_t *col_idx, int32_t n
     sms = std::max(sms, 1);
     c->blocks_cap = sms * 8;
     // the staged kernel is persistent: its grid (one block per SM) must fit
-    if (!(flags & F2V_FLAG_NO_STAGING) && n < (1 << 30) &&   // map rows (2n) are int32
-
+    // (its tensor map spans the Z buffers, 2n rows or 3n with a random
+    // partition, addressed by int32 row coordinates)
+    if (!(flags & F2V_FLAG_NO_STAGING) && (int64_t)n * (c->partition ? 3 : 2) <= INT32_MAX &&
         bulk_config(d, precision == F2V_BF16, &c->bulk_warps, &c->bulk_smem) &&
         bulk_resident(d, precision == F2V_BF16, c->bulk_warps, c->bulk_smem) >= 1) {
         c->bulk = true;
