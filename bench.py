@@ -239,16 +239,25 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
-    """The largest x of all ranks (each rank's time; the job's is the slowest)."""
+def _reduce_over_ranks(x: float, world: int, op: str) -> float:
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
     dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
     t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x of all ranks (each rank's time; the job's is the slowest)."""
+    return _reduce_over_ranks(x, world, "max")
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    """The sum of x over all ranks (work done by the whole job)."""
+    return _reduce_over_ranks(x, world, "sum")
 
 
 # --------------------------------------------------------------------------
@@ -673,6 +682,7 @@ def run_precision(args, world, rank, local):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        barrier(world)
         launches0 = ctx.launch_count
         with ClockSampler(local) as clk:
             ev0.record(stream)
@@ -680,7 +690,8 @@ def run_precision(args, world, rank, local):
                 ctx.epoch()
             ev1.record(stream)
             torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
+        barrier(world)
+        ms = max_over_ranks(ev0.elapsed_time(ev1), world)
         ctx.set_kernel_timing(True)
         ctx.read_kernel_timing()
         for _ in range(3):
@@ -691,23 +702,24 @@ def run_precision(args, world, rank, local):
         res[name] = {"ms_per_step": ms / args.steps, "P": P, "kernel_ms": kernel_ms / max(n_timed, 1),
                      "launches": ctx.launch_count - launches0, "clocks": clk.summary()}
         ctx.close()
-    # error against the FP64 oracle on a 10,000-vertex snowball sample
-    sub = graphs.induced_subgraph(g, snowball(g, 10000))
-    Z0 = oracle.init_embedding(sub.n, d, 1)
+    # error against the FP64 oracle on a 10,000-vertex snowball sample (rank 0)
     err = {}
-    for ep in (1, E):
-        want = oracle.train(model, sub.row_ptr, sub.col_idx, Z0, s, b, 1, lr, ep,
-                            schedule=1, total_epochs=E)
-        for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
-            with f2v.Context(sub.row_ptr, sub.col_idx, sub.n, d, model=model, s=s, lr=lr,
-                             minibatch=b, seed=1, precision=prec) as c2:
-                c2.set_schedule(f2v.LR_LINEAR, E)
-                c2.train(ep)
-                got = c2.embedding().astype(np.float64)
-            rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-3)
-            err[f"{name}_epochs{ep}"] = {"max_rel": float(rel.max()),
-                                         "median_rel": float(np.median(rel)),
-                                         "rms_abs": float(np.sqrt(np.mean((got - want) ** 2)))}
+    if rank == 0:
+        sub = graphs.induced_subgraph(g, snowball(g, 10000))
+        Z0 = oracle.init_embedding(sub.n, d, 1)
+        for ep in (1, E):
+            want = oracle.train(model, sub.row_ptr, sub.col_idx, Z0, s, b, 1, lr, ep,
+                                schedule=1, total_epochs=E)
+            for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
+                with f2v.Context(sub.row_ptr, sub.col_idx, sub.n, d, model=model, s=s, lr=lr,
+                                 minibatch=b, seed=1, precision=prec) as c2:
+                    c2.set_schedule(f2v.LR_LINEAR, E)
+                    c2.train(ep)
+                    got = c2.embedding().astype(np.float64)
+                rel = np.abs(got - want) / np.maximum(np.abs(want), 1e-3)
+                err[f"{name}_epochs{ep}"] = {"max_rel": float(rel.max()),
+                                             "median_rel": float(np.median(rel)),
+                                             "rms_abs": float(np.sqrt(np.mean((got - want) ** 2)))}
     peak, peak_kind = hbm_peak()
     bf = res["bf16"]
     alg = bf["P"] * d * 2
@@ -800,6 +812,7 @@ def run_served(args, world, rank, local):
     scales = rng.integers(10, 22, times.size)
     dsel = rng.integers(0, len(dims), times.size)
     ids = []
+    barrier(world)
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         for i, t in enumerate(times):
@@ -812,12 +825,12 @@ def run_served(args, world, rank, local):
     infos = [srv.info(j) for j in ids]
     done = [i for i in infos if i.state == f2v.JOB_DONE]
     lat = np.array([i.finish_s - i.submit_s for i in done]) if done else np.zeros(0)
-    pairs = st.pairs_done - base.pairs_done
-    window = max(t_end, 1e-9)
+    pairs = sum_over_ranks(float(st.pairs_done - base.pairs_done), world)
+    window = max_over_ranks(max(t_end, 1e-9), world)
     srv.close()        # jobs still running or queued are stopped
     pct = (lambda q: float(np.percentile(lat, q)) if lat.size else None)
-    offered = sum((pool[int(scales[i])].nnz + pool[int(scales[i])].n * 5) * SERVE_EPOCHS
-                  for i in range(times.size))
+    offered = sum_over_ranks(float(sum((pool[int(scales[i])].nnz + pool[int(scales[i])].n * 5)
+                                       * SERVE_EPOCHS for i in range(times.size))), world)
     if rank == 0:
         line = {
             "metric": "force-pair updates/s (served)", "value": pairs / window,

@@ -1,6 +1,6 @@
 """The multi-process paths of bench.py on CPU, with the gloo backend and two
-ranks: the max-over-ranks timing, and the reference arm, which only rank 0
-runs and prints."""
+ranks: the max-over-ranks timing and the sum of work over ranks, and the
+reference arm, which only rank 0 runs and prints."""
 import json
 import os
 import socket
@@ -27,17 +27,18 @@ def _worker(rank, world, port, out):
     import bench
     dist.init_process_group("gloo", rank=rank, world_size=world)
     bench.barrier(world)
-    out[rank] = bench.max_over_ranks(1.5 + rank, world)
+    out[rank] = (bench.max_over_ranks(1.5 + rank, world),
+                 bench.sum_over_ranks(10.0 * (rank + 1), world))
     dist.destroy_process_group()
 
 
-def test_max_over_ranks_two_gloo_ranks():
+def test_max_and_sum_over_two_gloo_ranks():
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
         mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True,
                            start_method="spawn")
-        assert dict(out) == {0: 2.5, 1: 2.5}
+        assert dict(out) == {0: (2.5, 30.0), 1: (2.5, 30.0)}
 
 
 def test_reference_arm_under_two_ranks_prints_once():
