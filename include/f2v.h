@@ -313,7 +313,12 @@ f2v_status f2v_read_kernel_timing(f2v_ctx *ctx, int64_t *launches, double *total
  *
  * All pointers are device memory owned by the caller: the CSR (row_ptr[n+1],
  * col_idx[nnz], with the rules of f2v_create, not re-checked here) and the
- * two FP32 embedding buffers (n x d, row-major).  It computes, for the
+ * two FP32 embedding buffers (n x d, row-major).  z_cur and z_next must
+ * start on a 16-byte boundary (8 bytes is enough for d = 2, and 4 for a d
+ * that is not a power of two from 4 to 1024), and row_ptr and col_idx on a
+ * 4-byte boundary: the kernel moves rows with vector loads and stores, so
+ * the call returns F2V_EINVAL, before any device work, for a pointer that
+ * is not aligned.  It computes, for the
  * vertices u in [mb_begin, mb_end), the same update as a context's epoch
  * `epoch` (negative samples from `seed`, learning rate `eta`): partner rows
  * v < mb_begin are read from z_next (already updated this epoch) and all
@@ -334,7 +339,9 @@ f2v_status f2v_read_kernel_timing(f2v_ctx *ctx, int64_t *launches, double *total
  * calls share the array: calls whose work overlaps on the GPU (other
  * streams, other host threads on the same device) race and give wrong
  * results.  The first call on each device looks up the array's address with
- * that device current; make it before any stream capture.  Errors are read
+ * that device current; make it before any stream capture.  The address is
+ * kept until the process exits, so after a cudaDeviceReset on a device this
+ * entry point must not be called on that device again.  Errors are read
  * with f2v_noalloc_last_error.
  */
 f2v_status f2v_minibatch_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n,

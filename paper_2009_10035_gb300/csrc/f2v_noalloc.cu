@@ -18,7 +18,11 @@
 // overlaps on the GPU (different streams, or different host threads on one
 // device) race on it and give wrong results.  The first call on a device
 // looks up the array's device address (cudaGetSymbolAddress) with that
-// device current; make that first call before any stream capture.
+// device current; make that first call before any stream capture.  The
+// address is kept for the life of the process: after a cudaDeviceReset (or
+// anything else that re-creates the device's primary context) the kept
+// address is stale, so this entry point must not be used on that device
+// again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -141,6 +145,19 @@ extern "C" f2v_status f2v_minibatch_noalloc(const int32_t *row_ptr, const int32_
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: a pointer is NULL");
     if (n < 1 || d < 1 || d > 1024 || s < 0 || s > 65534 || epoch < 0)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: n, d, s or epoch out of range");
+    // The kernel reads and writes rows of Z with VEC-wide vector accesses
+    // (16 bytes for most d, 8 for d = 2), and the CSR as 4-byte words.  The
+    // buffers come from the caller's own allocator, so a misaligned pointer
+    // is possible here; it would fault on the GPU, so it is refused first.
+    const Shape sh = choose_shape(d);
+    const uintptr_t zalign = (uintptr_t)(sh.VEC * sizeof(float));
+    if (((uintptr_t)z_cur % zalign) != 0 || ((uintptr_t)z_next % zalign) != 0)
+        return noalloc_fail(F2V_EINVAL,
+                            "f2v_minibatch_noalloc: z_cur and z_next must be aligned to "
+                            "16 bytes (8 for d = 2, 4 for d not in {2,4,8,...,1024})");
+    if (((uintptr_t)row_ptr % 4) != 0 || ((uintptr_t)col_idx % 4) != 0)
+        return noalloc_fail(F2V_EINVAL,
+                            "f2v_minibatch_noalloc: row_ptr and col_idx must be 4-byte aligned");
     if (model < F2V_TDIST || model > F2V_FORCEATLAS)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: unknown model");
     if (!(eta > 0.f) || eta != eta || eta > 3.0e38f)
@@ -148,7 +165,6 @@ extern "C" f2v_status f2v_minibatch_noalloc(const int32_t *row_ptr, const int32_
     if (mb_begin < 0 || mb_end > n || mb_begin >= mb_end)
         return noalloc_fail(F2V_EINVAL, "f2v_minibatch_noalloc: need 0 <= mb_begin < mb_end <= n");
     cudaStream_t st = (cudaStream_t)stream;
-    const Shape sh = choose_shape(d);
     const int C = items_pairs(sh);
     const int mb_count = mb_end - mb_begin;
     // the kernel's decode window reads the pair prefix up to 32 vertices past

@@ -118,3 +118,39 @@ def test_output_buffers_are_checked_before_the_call():
             f2v._host_out(out, 12)
     with pytest.raises(ValueError):
         f2v._host_out(np.zeros(11, np.float32), 12, exact=False)
+
+
+@pytest.mark.parametrize("d,zoff,csr_off,ok", [
+    (128, 8, 0, False),      # 16-byte vectors: an 8-byte offset is refused
+    (128, 4, 0, False),
+    (2, 4, 0, False),        # 8-byte vectors at d = 2
+    (128, 0, 2, False),      # CSR words must be 4-byte aligned
+    (2, 8, 0, True),         # 8 bytes is enough at d = 2 (passes the check)
+    (48, 4, 0, True),        # scalar shape: 4 bytes is enough (passes the check)
+])
+def test_noalloc_rejects_misaligned_buffers_before_device_work(lib, d, zoff, csr_off, ok):
+    """f2v_minibatch_noalloc takes Z and the CSR from the caller's allocator;
+    a pointer that the kernel's vector accesses cannot use is refused on the
+    host.  The pointers here are never dereferenced: the call must return
+    before any device work (a call that passes the alignment check then
+    fails later with another message, since mb_begin >= mb_end)."""
+    base = 1 << 20
+    rc = lib.f2v_minibatch_noalloc(
+        ctypes.c_void_p(base + csr_off), ctypes.c_void_p(base + 4096 + csr_off), 10, d, 0, 5,
+        ctypes.c_float(0.02), 1, 0, 3, 3 if ok else 4,
+        ctypes.c_void_p(base + 8192 + zoff), ctypes.c_void_p(base + 65536 + zoff), None)
+    assert rc == f2v.EINVAL
+    msg = lib.f2v_noalloc_last_error().decode()
+    if ok:
+        assert "aligned" not in msg and "mb_begin" in msg
+    else:
+        assert "aligned" in msg
+
+
+def test_library_rebuild_depends_on_every_header():
+    """An edit to any public header makes the library out of date."""
+    import os
+    deps = set(build._deps())
+    for h in os.listdir(build.INCLUDE):
+        if h.endswith(".h"):
+            assert os.path.join(build.INCLUDE, h) in deps, h
