@@ -224,6 +224,22 @@ f2v_status f2v_set_stream(f2v_ctx *ctx, void *stream);
 f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
                         const int32_t *neg_pairs, int64_t nneg, double *auc);
 
+/*
+ * The loss of Eq. 2 on the current Z, in FP64 on the device: *loss = the sum
+ * over all vertices u of L(u) = sum over the neighbours v of u (the CSR as
+ * given to f2v_create) of -log delta(z_u, z_v), plus the sum over u's s
+ * negative samples w of epoch `epoch` (Philox(ctr = (u, epoch, k, 0)).x0 mod
+ * n, k < s; a sample equal to u adds nothing) of -log(1 - delta(z_u, z_w)).
+ * delta is Eq. 3's sigma(z_u . z_x) for the sigmoid model and Eq. 7's
+ * 1/(1 + |z_u - z_x|^2) for the t model, with |z_u - z_w|^2 floored at 1e-8
+ * in the repulsive term as in training.  Rows are read as stored (the FP32
+ * master in the BF16 form) and every product, sum and logarithm is FP64;
+ * the pairs are summed in a fixed order, so the result is reproducible.
+ * F2V_EINVAL for the other force models (the paper gives no loss for them)
+ * or epoch < 0.  Synchronous.
+ */
+f2v_status f2v_eval_loss(f2v_ctx *ctx, int32_t epoch, double *loss);
+
 /* Negative samples the device draws in epoch `epoch`: out[u*s + k] for all
    u < n, k < s (count must equal n*s).  With F2V_FLAG_SHARED_SAMPLES row u
    is the set of u's minibatch in that epoch (under F2V_FLAG_RANDOM_PARTITION,

@@ -114,6 +114,10 @@ namespace f2v {
 cudaError_t eval_auc_device(const float *zf, const __nv_bfloat16 *zb, int d, int model,
                             const int32_t *pos, int64_t npos, const int32_t *neg, int64_t nneg,
                             cudaStream_t st, double *auc, std::string *err);
+cudaError_t eval_loss_device(const float *z, int d, int model, const int32_t *row_ptr,
+                             const int32_t *col_idx, int n, int64_t nnz, int s, uint32_t epoch,
+                             uint32_t key0, uint32_t key1, cudaStream_t st, double *loss,
+                             std::string *err);
 }
 
 // One epoch's random partition: its order, the graph relabelled into it and
@@ -1376,6 +1380,29 @@ f2v_status f2v_eval_auc(f2v_ctx *ctx, const int32_t *pos_pairs, int64_t npos,
     ctx->launches += 3;
     if (e == cudaErrorMemoryAllocation) return fail(ctx, F2V_ENOMEM, "eval_auc: %s", err.c_str());
     if (e != cudaSuccess) return fail(ctx, F2V_ECUDA, "eval_auc: %s", err.c_str());
+    return F2V_OK;
+}
+
+f2v_status f2v_eval_loss(f2v_ctx *ctx, int32_t epoch, double *loss)
+{
+    F2V_CHECK_CTX(ctx);
+    if (!loss) return fail(ctx, F2V_EINVAL, "loss is NULL");
+    if (epoch < 0) return fail(ctx, F2V_EINVAL, "epoch < 0");
+    if (ctx->model != F2V_TDIST && ctx->model != F2V_SIGMOID)
+        return fail(ctx, F2V_EINVAL,
+                    "eval_loss: the loss of Eq. 2 is defined for the t and sigmoid models only");
+    DeviceGuard g(ctx->device);
+    f2v_status st = sync_current(ctx);
+    if (st != F2V_OK) return st;
+    std::string err;
+    const float *zf = ctx->precision == F2V_BF16 ? ctx->master : (const float *)ctx->z[ctx->cur];
+    // the graph as given (with a random partition the kernels walk a relabelled copy)
+    cudaError_t e = eval_loss_device(zf, ctx->d, ctx->model, ctx->row_ptr0, ctx->col_idx0, ctx->n,
+                                     ctx->nnz, ctx->s, (uint32_t)epoch, (uint32_t)ctx->seed,
+                                     (uint32_t)(ctx->seed >> 32), ctx->stream, loss, &err);
+    ctx->launches += 2;
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, F2V_ENOMEM, "eval_loss: %s", err.c_str());
+    if (e != cudaSuccess) return fail(ctx, F2V_ECUDA, "eval_loss: %s", err.c_str());
     return F2V_OK;
 }
 

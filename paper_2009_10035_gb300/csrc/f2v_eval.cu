@@ -1,4 +1,5 @@
-// f2v_eval.cu -- held-out-edge link-prediction AUC on the device.
+// f2v_eval.cu -- held-out-edge link-prediction AUC and the loss of Eq. 2 on
+// the device, both in FP64.
 //
 // Scores are FP64: z_u . z_v for the sigmoid model, -||z_u - z_v||^2 for the
 // t model (both monotone in the model's similarity delta, Eq. 3 / Eq. 7).
@@ -10,7 +11,11 @@
 
 #include <cub/device/device_radix_sort.cuh>
 
+#include <stdint.h>
+
 #include <string>
+
+#include "f2v_device.cuh"
 
 namespace f2v {
 
@@ -64,7 +69,137 @@ __global__ void count_kernel(const double *pos, int64_t npos, const double *neg_
     if ((threadIdx.x & 31) == 0 && local) atomicAdd(total, local);
 }
 
+// ---- loss of Eq. 2 --------------------------------------------------------
+
+constexpr int kLossBlocks = 1024;    // fixed grid: the summation order does not
+constexpr int kLossThreads = 256;    // depend on the device
+
+// -log delta(z_u, z_x) of a neighbour (attractive) or -log(1 - delta) of a
+// negative sample, from r = z_u . z_x (sigmoid model, delta of Eq. 3) or
+// r = |z_u - z_x|^2 (t model, delta of Eq. 7, t^2 floored at 1e-8 in the
+// repulsive term).  log(1 + e^y) is evaluated as max(y, 0) + log1p(e^-|y|),
+// which is the same value without overflow.
+__device__ __forceinline__ double pair_loss(int model, bool attractive, double r)
+{
+    if (model == 1) {
+        const double y = attractive ? -r : r;   // -log sigma(r), -log(1 - sigma(r))
+        return fmax(y, 0.0) + log1p(exp(-fabs(y)));
+    }
+    if (attractive) return log1p(r);            // -log 1/(1 + t^2)
+    const double t2 = fmax(r, 1e-8);
+    return log1p(1.0 / t2);                     // -log t^2/(1 + t^2)
+}
+
+// Pairs of the loss: CSR entry p < nnz is (u, col_idx[p]) with u the row
+// holding p; p = nnz + u * s + k is negative sample k of u.  Each warp takes
+// 32 consecutive pairs, decoded one per lane, and evaluates them in turn with
+// its lanes striding over the d elements; lane j keeps pair j's term.  Each
+// block writes the FP64 sum of its terms, reduced in a fixed order.
+__global__ void __launch_bounds__(kLossThreads)
+    loss_kernel(const float *z, int d, int model, const int32_t *row_ptr, const int32_t *col_idx,
+                int n, int64_t nnz, int s, uint32_t epoch, uint32_t key0, uint32_t key1,
+                double *partial)
+{
+    __shared__ double red[kLossThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = nnz + (int64_t)n * s;
+    double acc = 0.0;
+    for (int64_t base = warp * 32; base < total; base += nwarps * 32) {
+        const int64_t p = base + lane;
+        int u = -1, x = -1;
+        if (p < nnz) {
+            int lo = 0, hi = n - 1;                  // the row holding entry p
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)row_ptr[mid] <= p) lo = mid; else hi = mid - 1;
+            }
+            u = lo;
+            x = col_idx[p];
+        } else if (p < total) {
+            const int64_t q = p - nnz;
+            u = (int)(q / s);
+            const uint32_t k = (uint32_t)(q - (int64_t)u * s);
+            x = (int)(philox_x0((uint32_t)u, epoch, k, 0u, key0, key1) % (uint32_t)n);
+            if (x == u) x = -1;                      // a sample equal to u adds nothing
+        }
+        const bool attr = p < nnz;
+        for (int j = 0; j < 32; ++j) {
+            const int uj = __shfl_sync(0xffffffffu, u, j);
+            const int xj = __shfl_sync(0xffffffffu, x, j);
+            if (uj < 0 || xj < 0) continue;          // warp-uniform
+            const float *a = z + (int64_t)uj * d;
+            const float *b = z + (int64_t)xj * d;
+            double r = 0.0;
+            for (int e = lane; e < d; e += 32) {
+                const double ae = (double)a[e], be = (double)b[e];
+                if (model == 1) {
+                    r = fma(ae, be, r);
+                } else {
+                    const double df = ae - be;
+                    r = fma(df, df, r);
+                }
+            }
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) r += __shfl_xor_sync(0xffffffffu, r, m);
+            if (lane == j) acc += pair_loss(model, attr, r);
+        }
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    if (lane == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kLossThreads / 32; ++i) t += red[i];
+        partial[blockIdx.x] = t;
+    }
+}
+
+// out = sum of partial[0 .. count), in a fixed order (one block).
+__global__ void sum_kernel(const double *partial, int count, double *out)
+{
+    __shared__ double red[kLossThreads];
+    double t = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) t += partial[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w >= 1; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+cudaError_t eval_loss_device(const float *z, int d, int model, const int32_t *row_ptr,
+                             const int32_t *col_idx, int n, int64_t nnz, int s, uint32_t epoch,
+                             uint32_t key0, uint32_t key1, cudaStream_t st, double *loss,
+                             std::string *err)
+{
+    double *partial = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&partial, sizeof(double) * (kLossBlocks + 1), st);
+    if (e != cudaSuccess) {
+        *err = std::string("alloc: ") + cudaGetErrorString(e);
+        return e;
+    }
+    loss_kernel<<<kLossBlocks, kLossThreads, 0, st>>>(z, d, model, row_ptr, col_idx, n, nnz, s,
+                                                      epoch, key0, key1, partial);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        sum_kernel<<<1, kLossThreads, 0, st>>>(partial, kLossBlocks, partial + kLossBlocks);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(loss, partial + kLossBlocks, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) *err = std::string("loss kernels: ") + cudaGetErrorString(e);
+    cudaFreeAsync(partial, st);
+    cudaStreamSynchronize(st);
+    return e;
+}
 
 cudaError_t eval_auc_device(const float *zf, const __nv_bfloat16 *, int d, int model,
                             const int32_t *pos, int64_t npos, const int32_t *neg, int64_t nneg,

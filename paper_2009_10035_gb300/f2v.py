@@ -84,6 +84,7 @@ def signatures() -> dict:
         "f2v_get_epoch": ([vp, ctypes.POINTER(i32)], st),
         "f2v_set_stream": ([vp, vp], st),
         "f2v_eval_auc": ([vp, vp, i64, vp, i64, ctypes.POINTER(ctypes.c_double)], st),
+        "f2v_eval_loss": ([vp, i32, ctypes.POINTER(ctypes.c_double)], st),
         "f2v_debug_samples": ([vp, i32, vp, sz], st),
         "f2v_debug_walks": ([vp, i32, vp, sz], st),
         "f2v_debug_wait": ([vp, i32], st),
@@ -300,6 +301,13 @@ class Context:
         out = ctypes.c_double()
         self._check(self._lib.f2v_eval_auc(self._h, _ptr(pos), pos.shape[0], _ptr(neg),
                                            neg.shape[0], ctypes.byref(out)))
+        return out.value
+
+    def eval_loss(self, epoch: int) -> float:
+        """The loss of Eq. 2 (Eq. 3 / Eq. 7) on the current Z in FP64, with
+        the negative samples of `epoch`."""
+        out = ctypes.c_double()
+        self._check(self._lib.f2v_eval_loss(self._h, int(epoch), ctypes.byref(out)))
         return out.value
 
     def debug_samples(self, epoch: int) -> np.ndarray:
