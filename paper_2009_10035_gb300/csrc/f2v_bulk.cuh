@@ -46,6 +46,9 @@
 namespace f2v {
 
 constexpr int kOwnSlots = 4;                 // distinct vertices per tile at most
+// A tile finishes at most kOwnSlots + 1 vertices (the one it continues, the
+// ones it holds, and at a chunk's end its last).
+constexpr int kMaxPub = kOwnSlots + 1;
 // own rows arrive by tile::gather4 copies of four rows each into a buffer of
 // kOwnSlots rows, so the buffer must hold whole copies
 static_assert(kOwnSlots % 4 == 0 && kOwnSlots <= 8, "kOwnSlots: a multiple of 4, at most 8");
@@ -121,6 +124,23 @@ __device__ __forceinline__ void fence_mbar_init()
 }
 
 
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(int32_t *p, int32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int atom_add_relaxed_gpu(int32_t *p, int32_t v)
+{
+    int r;
+    asm volatile("atom.relaxed.gpu.global.add.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    return r;
+}
+
 // Bounded wait on an mbarrier phase; false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
@@ -144,7 +164,9 @@ struct BulkLayout {
     static constexpr int VERT_OFF = COEF_OFF + 32 * 4;             // int[32]: vertex - u_tile
     static constexpr int VEND_OFF = VERT_OFF + 32 * 4;             // int[32]: vertex end
     static constexpr int BAR_OFF = VEND_OFF + 32 * 4;              // uint64
-    static constexpr int BYTES = ((BAR_OFF + 8 + 127) / 128) * 128;
+    // the tile's finished vertices whose flags are pending (kMaxPub ids)
+    static constexpr int PEND_OFF = BAR_OFF + 8;
+    static constexpr int BYTES = ((PEND_OFF + 4 * kMaxPub + 127) / 128) * 128;
 };
 
 // One chunk of one minibatch.
@@ -249,6 +271,35 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
     return t;
 }
 
+// Finishing vertices.  A vertex whose pairs all lie in the tile's chunk gets
+// its new row stored at once, but its flag is set only after the tile: one
+// release fence then covers every row the tile stored, and the flags (and the
+// chunk's completion count) follow with relaxed stores.  A release fence
+// waits for the warp's stores to reach L2, which costs about as much as a
+// tile's arithmetic, so one per tile instead of one per vertex pays.  A vertex
+// split across chunks arrives at its combine-tree counter at once: the
+// arrival decides which part completes the vertex, and delaying it delays
+// every later minibatch that reads the row.
+
+// Vertex u (local pairs [vbeg, vend), summed in g over level-0 unit
+// `unit0`) ends: if the unit held all its pairs, store z_u - eta g (Eq. 10)
+// and list u for its flag; else pass its part up the combine tree
+// (finish_vertex, which releases it and may complete the vertex).
+template <int VEC, int NV, int MODEL, typename Ts>
+__device__ __forceinline__ void finish_store(const ForceArgs<Ts> &a, const FinishCtx &fc, int lane,
+                                             int unit0, int u, int vbeg, int vend,
+                                             const float *zu, float *g, int *pend, int &npub)
+{
+    if (vbeg / fc.C == (vend - 1) / fc.C) {
+        const FinishCtx quiet{fc.C, fc.slots, fc.unit_cnt, nullptr, 0};
+        write_row<32, VEC, NV, true, MODEL>(a, quiet, 0xffffffffu, u, lane, zu, g);
+        if (lane == 0) pend[npub] = u;
+        ++npub;
+        return;
+    }
+    finish_vertex<32, VEC, NV, true, MODEL>(a, fc, 0xffffffffu, lane, unit0, u, vbeg, vend, zu, g);
+}
+
 template <int D, typename Ts, int MODEL>
 __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 384)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
@@ -270,6 +321,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
     int *vert = reinterpret_cast<int *>(wsm + Lay::VERT_OFF);
     int *vends = reinterpret_cast<int *>(wsm + Lay::VEND_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(wsm + Lay::BAR_OFF);
+    int *pend = reinterpret_cast<int *>(wsm + Lay::PEND_OFF);
     // the force model class, fixed per instantiation: every model but the
     // sigmoid reduces a squared distance and accumulates c (z_u - x)
     constexpr bool tdist = (MODEL != 1);
@@ -292,6 +344,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
     if (!find_chunk(a, lane, a.k_begin, ch)) return;
     Tile t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
     bool chunk_start = true;
+    int ring_known = a.k_begin - 1;    // minibatches up to this one are known complete
     int ucur = -1, vbeg = 0, vend = 0;
     float zu[EPL], g[EPL];
     // t model: the sum of c * (z_u - x) is kept as the sum of -c * x plus
@@ -306,8 +359,11 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
         // ---- minibatch entry: the scratch region must be free ------------
         if (chunk_start) {
             chunk_start = false;
-            if (ch.k - a.ring >= a.k_begin) {
+            // (a warp's chunks come in minibatch order, so a region seen free
+            // for one chunk stays free for the warp's later chunks)
+            if (ch.k - a.ring >= a.k_begin && ch.k - a.ring > ring_known) {
                 const int kk = ch.k - a.ring;
+                ring_known = kk;
                 const int target =
                     (int)(__ldg(&a.mb_item_base[kk + 1]) - __ldg(&a.mb_item_base[kk]));
                 int ok = 1;
@@ -468,6 +524,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
         const FinishCtx fc{cur.C, a.slots + (int64_t)ring_slot * a.slot_stride,
                            a.unit_cnt + (int64_t)ring_slot * a.cnt_stride, a.row_flag,
                            flag_value};
+        int npub = 0;                  // this tile's rows whose flags are pending
         unsigned starts = seg_starts;
         while (starts) {
             const int rs = __ffs(starts) - 1;
@@ -480,8 +537,8 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
 #pragma unroll
                         for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
                     }
-                    finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx,
-                                                            ucur, vbeg, vend, zu, g);
+                    finish_store<VEC, NV, MODEL>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu, g,
+                                                 pend, npub);
                 }
                 csum = 0.f;
                 vbeg = (ucur >= 0) ? vend : first_lo;
@@ -548,14 +605,21 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
                 for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
             }
             csum = 0.f;
-            finish_vertex<32, VEC, NV, true, MODEL>(a.f, fc, 0xffffffffu, lane, cur.idx, ucur,
-                                                    vbeg, vend, zu, g);
+            finish_store<VEC, NV, MODEL>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu, g, pend,
+                                         npub);
             ucur = -1;
-            __syncwarp();
-            if (lane == 0)
-                asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(&a.mb_done[cur.k])
-                             : "memory");
             chunk_start = true;
+        }
+        // ---- publish: one release fence for everything the tile stored ---
+        if (npub > 0 || last_of_chunk) {
+            __syncwarp();
+            fence_acq_rel_gpu();
+            if (lane < npub) st_relaxed_gpu(&a.row_flag[pend[lane]], flag_value);
+            // the chunk is done: its rows, its tree parts and any tree sums it
+            // made (with their counter resets) precede the fence
+            if (last_of_chunk && lane == 0)
+                asm volatile("red.relaxed.gpu.global.add.s32 [%0], 1;" ::"l"(&a.mb_done[cur.k])
+                             : "memory");
         }
         __syncwarp();
         if (!more) break;
