@@ -141,6 +141,70 @@ __device__ __forceinline__ int atom_add_relaxed_gpu(int32_t *p, int32_t v)
     return r;
 }
 
+// Packed FP32 pairs (sm_100 family): one instruction for two elements, each
+// rounded as its scalar counterpart (fmaf, subtraction) would be.
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rd, {%0, %1};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rd;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+__device__ __forceinline__ void sub2(float &d0, float &d1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// A lane's part of a pair's reduced scalar over its EPL elements: the squared
+// distance (tdist) or the dot product of its own-row and partner slices.
+// PACKED: as two interleaved partial sums (even and odd elements) added at the
+// end, with packed instructions; else one sequential sum.  (Packed halves the
+// instructions but holds more registers: it is faster except for FP32 rows
+// with a distance model, where it made the kernel spill.)
+template <int EPL, bool TDIST, bool PACKED>
+__device__ __forceinline__ float lane_reduce(const float *o, const float *x)
+{
+    if (!PACKED) {
+        float acc = 0.f;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+            if (TDIST) {
+                const float df = o[e] - x[e];
+                acc = fmaf(df, df, acc);
+            } else {
+                acc = fmaf(o[e], x[e], acc);
+            }
+        }
+        return acc;
+    }
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPL; e += 2) {
+        if (TDIST) {
+            float d0, d1;
+            sub2(d0, d1, o[e], o[e + 1], x[e], x[e + 1]);
+            fma2(s0, s1, d0, d1, d0, d1);
+        } else {
+            fma2(s0, s1, o[e], o[e + 1], x[e], x[e + 1]);
+        }
+    }
+    return s0 + s1;
+}
+
+// acc += c * x, element by element.
+template <int EPL>
+__device__ __forceinline__ void lane_axpy(float *acc, float c, const float *x)
+{
+#pragma unroll
+    for (int e = 0; e < EPL; e += 2) fma2(acc[e], acc[e + 1], c, c, x[e], x[e + 1]);
+}
+
 // Bounded wait on an mbarrier phase; false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
@@ -301,7 +365,7 @@ __device__ __forceinline__ void finish_store(const ForceArgs<Ts> &a, const Finis
 }
 
 template <int D, typename Ts, int MODEL>
-__global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 384)
+__global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
                       const __grid_constant__ CUtensorMap mmap)
@@ -325,6 +389,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
     // the force model class, fixed per instantiation: every model but the
     // sigmoid reduces a squared distance and accumulates c (z_u - x)
     constexpr bool tdist = (MODEL != 1);
+    constexpr bool kPackReduce = !(tdist && sizeof(Ts) == 4);
     const int model = model_of<MODEL>(a.f.model);
     const int flag_value = (int)a.f.epoch + 1;
 
@@ -462,18 +527,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
 #pragma unroll
                 for (int i = 0; i < NV; ++i)
                     load_vec_smem<VEC>(rows + r * D + (i * L + lane) * VEC, x + i * VEC);
-                float acc = 0.f;
-                if (tdist) {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const float df = o[e] - x[e];
-                        acc = fmaf(df, df, acc);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) acc = fmaf(o[e], x[e], acc);
-                }
-                p[r] = acc;
+                p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
             }
         } else {
 #pragma unroll
@@ -486,18 +540,7 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
                     load_vec_smem<VEC>(rows + r * D + e0, x + i * VEC);
                     load_vec_smem<VEC>(own + j * D + e0, o + i * VEC);
                 }
-                float acc = 0.f;
-                if (tdist) {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) {
-                        const float df = o[e] - x[e];
-                        acc = fmaf(df, df, acc);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < EPL; ++e) acc = fmaf(o[e], x[e], acc);
-                }
-                p[r] = acc;
+                p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
             }
         }
 #pragma unroll
@@ -564,14 +607,8 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
                     for (int k = 0; k < NV; ++k)
                         load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
                     float *acc = (r & 1) ? g2 : g;
-                    if (tdist) {
-                        csum += c;
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(-c, x[e], acc[e]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
-                    }
+                    if (tdist) csum += c;
+                    lane_axpy<EPL>(acc, tdist ? -c : c, x);
                 }
             } else {
                 for (int r0 = rs; r0 < re; r0 += 4) {
@@ -584,14 +621,8 @@ __global__ void __launch_bounds__((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 5
                         for (int k = 0; k < NV; ++k)
                             load_vec_smem<VEC>(rows + r * D + (k * L + lane) * VEC, x + k * VEC);
                         float *acc = (i & 1) ? g2 : g;
-                        if (tdist) {
-                            csum += c;
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e) acc[e] = fmaf(-c, x[e], acc[e]);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < EPL; ++e) acc[e] = fmaf(c, x[e], acc[e]);
-                        }
+                        if (tdist) csum += c;
+                        lane_axpy<EPL>(acc, tdist ? -c : c, x);
                     }
                 }
             }
@@ -632,10 +663,11 @@ template <int D, typename Ts>
 int bulk_warps()
 {
     const int w = kBulkSmemBudget / BulkLayout<D, Ts>::BYTES;
-    // the kernel's launch bound: 16 warps where the registers allow (BF16 rows
-    // halve the staging buffers, so d = 128 BF16 fits 16 warps per SM), else
-    // 12 (FP32 rows at d = 128: 18.5 KB of staging per warp, 222 KB per block)
-    const int cap = ((D <= 64 || (D <= 128 && sizeof(Ts) == 2)) ? 512 : 384) / 32;
+    // the kernel's launch bound: 16 warps at d = 64, else 12 (FP32 rows at
+    // d = 128: 18.5 KB of staging per warp, 222 KB per block).  BF16 rows at
+    // d = 128 would fit 16 warps, but 12 with 168 registers each measured
+    // faster (fewer, longer chunks; no spills)
+    const int cap = ((D <= 64) ? 512 : 384) / 32;
     return w > cap ? cap : w;
 }
 

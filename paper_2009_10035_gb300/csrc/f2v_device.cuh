@@ -53,6 +53,17 @@ __device__ __forceinline__ float z0_value(uint32_t i, uint32_t j, uint32_t k0, u
     return (float)(x >> 8) * 5.9604644775390625e-8f - 0.5f;   // 2^-24
 }
 
+// BF16 -> FP32 is exact: a BF16 value is the upper 16 bits of the FP32 value
+// with the same bits.  Widening by shift and mask keeps the conversion on the
+// integer ALUs, which issue at the FMA rate (a conversion instruction per
+// element would run at a fraction of it and, with two conversions per element
+// per tile, bound the BF16 kernels).
+__device__ __forceinline__ void bf16x2_to_float(unsigned int w, float *x)
+{
+    x[0] = __uint_as_float(w << 16);
+    x[1] = __uint_as_float(w & 0xFFFF0000u);
+}
+
 // Row element loads: VEC consecutive elements starting at p, widened to FP32.
 template <int VEC>
 __device__ __forceinline__ void load_vec(const float *p, float *x)
@@ -73,15 +84,13 @@ __device__ __forceinline__ void load_vec(const __nv_bfloat16 *p, float *x)
 {
     if constexpr (VEC == 4) {
         const uint2 t = __ldg(reinterpret_cast<const uint2 *>(p));
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
-        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+        bf16x2_to_float(t.x, x);
+        bf16x2_to_float(t.y, x + 2);
     } else if constexpr (VEC == 2) {
         const unsigned int t = __ldg(reinterpret_cast<const unsigned int *>(p));
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
-        x[0] = a.x; x[1] = a.y;
+        bf16x2_to_float(t, x);
     } else {
-        x[0] = __bfloat162float(p[0]);
+        x[0] = __uint_as_float((unsigned int)__ldg(reinterpret_cast<const unsigned short *>(p)) << 16);
     }
 }
 
@@ -105,13 +114,11 @@ __device__ __forceinline__ void load_vec_cg(const __nv_bfloat16 *p, float *x)
 {
     if constexpr (VEC == 4) {
         const uint2 t = __ldcg(reinterpret_cast<const uint2 *>(p));
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
-        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+        bf16x2_to_float(t.x, x);
+        bf16x2_to_float(t.y, x + 2);
     } else if constexpr (VEC == 2) {
         const unsigned int t = __ldcg(reinterpret_cast<const unsigned int *>(p));
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
-        x[0] = a.x; x[1] = a.y;
+        bf16x2_to_float(t, x);
     } else {
         const unsigned short t = __ldcg(reinterpret_cast<const unsigned short *>(p));
         x[0] = __uint_as_float((unsigned int)t << 16);
@@ -181,15 +188,13 @@ __device__ __forceinline__ void load_vec_smem(const __nv_bfloat16 *p, float *x)
 {
     if constexpr (VEC == 4) {
         const uint2 t = *reinterpret_cast<const uint2 *>(p);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.x));
-        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t.y));
-        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+        bf16x2_to_float(t.x, x);
+        bf16x2_to_float(t.y, x + 2);
     } else if constexpr (VEC == 2) {
         const unsigned int t = *reinterpret_cast<const unsigned int *>(p);
-        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&t));
-        x[0] = a.x; x[1] = a.y;
+        bf16x2_to_float(t, x);
     } else {
-        x[0] = __bfloat162float(p[0]);
+        x[0] = __uint_as_float((unsigned int)*reinterpret_cast<const unsigned short *>(p) << 16);
     }
 }
 
