@@ -583,12 +583,20 @@ int orc_train(int model, int64_t n, int32_t d,
 /* Loss (Eq. 2 with Eq. 3 / Eq. 7) and evaluation                       */
 /* ------------------------------------------------------------------ */
 
+/* log(1 + e^y), written so that e^y cannot overflow: for y > 0 it is
+   y + log(1 + e^-y).  (With coordinates bounded by 4 and d = 128 a dot
+   product reaches 2048, where e^y is infinite in FP64.) */
+static double log1p_exp(double y)
+{
+    return y > 0.0 ? y + log1p(exp(-y)) : log1p(exp(y));
+}
+
 /* -log delta(z_u, z_v) for a neighbour v */
 static double attractive_loss(int model, const double *zu, const double *zv, int32_t d)
 {
     if (model == ORC_SIGMOID) {
         const double x = dot(zu, zv, d);
-        return log(1.0 + exp(-x));                      /* Eq. 3, first sum */
+        return log1p_exp(-x);                           /* Eq. 3, first sum: -log sigma(x) */
     }
     const double t = dist(zu, zv, d);
     return log(1.0 + t * t);                            /* Eq. 7, first sum */
@@ -599,7 +607,7 @@ static double repulsive_loss(int model, const double *zu, const double *zw, int3
 {
     if (model == ORC_SIGMOID) {
         const double x = dot(zu, zw, d);
-        return -log(exp(-x) / (1.0 + exp(-x)));         /* Eq. 3, second sum */
+        return log1p_exp(x);                            /* Eq. 3, second sum: -log(1 - sigma(x)) */
     }
     const double t = dist(zu, zw, d);
     double t2 = t * t;

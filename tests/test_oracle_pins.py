@@ -415,3 +415,24 @@ def test_sigmoid_coordinates_are_bounded_t_model_is_not():
     zs2 = oracle.train(1, rp, ci, np.array([[0.3], [-0.2]]), 0, 2, 1, 0.5, 1)
     g_u = (1.0 / (1.0 + math.exp(0.06)) - 1.0) * -0.2
     assert abs(zs2[0, 0] - (0.3 - 0.5 * g_u)) < 1e-12
+
+
+def test_sigmoid_loss_stays_finite_at_the_coordinate_bound():
+    """Eq. 3's terms at dot products far beyond FP64's exp range: with every
+    coordinate at the bound 4 and d = 128, z_u . z_w = 2048, so the repulsive
+    term -log(1 - sigma(2048)) = log(1 + e^2048) equals 2048 to FP64
+    precision and the attractive -log sigma(2048) = log(1 + e^-2048) is 0
+    (e^-2048 underflows); at -2048 the roles swap."""
+    d = 128
+    Z = np.full((2, d), 4.0)
+    edge = graphs.from_edges(2, [0], [1])
+    none = graphs.from_edges(2, [], [])
+    rep = oracle.loss_vertex(oracle.SIGMOID, none.row_ptr, none.col_idx, Z, 0, 0, 1, 0,
+                             injected=[[1], []])
+    att = oracle.loss_vertex(oracle.SIGMOID, edge.row_ptr, edge.col_idx, Z, 0, 0, 1, 0)
+    assert rep == 2048.0 and att == 0.0
+    Z[1] = -4.0
+    rep = oracle.loss_vertex(oracle.SIGMOID, none.row_ptr, none.col_idx, Z, 0, 0, 1, 0,
+                             injected=[[1], []])
+    att = oracle.loss_vertex(oracle.SIGMOID, edge.row_ptr, edge.col_idx, Z, 0, 0, 1, 0)
+    assert rep == 0.0 and att == 2048.0
