@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true", help="no CPU-oracle baseline leg")
     ap.add_argument("--skip-e2e", action="store_true", help="no end-to-end leg")
     ap.add_argument("--skip-extra", action="store_true", help="no second force model")
+    ap.add_argument("--skip-quality", action="store_true",
+                    help="no held-out AUC / loss after the workload's epochs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["single", "batched", "served", "precision"],
                     default="single",
@@ -358,7 +360,9 @@ def run_ours(args, g, world, rank, local):
     stream = torch.cuda.current_stream()
     d, s, b, seed, lr = 128, 5, 4096, 1, 0.02
     model = MODEL_IDS[args.model]
-    total_epochs = max(20, args.warmup + args.steps)
+    # the schedule spans every epoch the context runs (warm-up, the timed
+    # epochs and the kernel-timed ones), so eta stays positive throughout
+    total_epochs = max(20, args.warmup + 2 * args.steps)
     flags = (f2v.FLAG_SHARED_SAMPLES if args.shared_samples else 0) | \
         (f2v.FLAG_RANDOM_PARTITION if args.random_partition else 0)
 
@@ -476,6 +480,13 @@ def run_ours(args, g, world, rank, local):
                        "copy Z to pinned host memory",
                "ms_per_job": 1e3 * dt / reps}
 
+    # ---- quality: held-out AUC and the loss of Eq. 2 after the workload's
+    # 20 epochs, reduced in FP64 on the device, beside the FP64 oracle's
+    quality = None
+    if not args.skip_quality:
+        quality = {name: single_quality(g, args, MODEL_IDS[name], stream, flags)
+                   for name in ([args.model] + [k for k in extra])}
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         rate, pairs, mbs, threads, el = oracle_rate(g, model, args.cpu_seconds, walk=args.walk,
@@ -493,9 +504,41 @@ def run_ours(args, g, world, rank, local):
             "config": workload_config(g, args),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "pairs_per_step": P, "also": extra,
+            "pairs_per_step": P, "also": extra, "quality": quality,
         }
         print(json.dumps(line), flush=True)
+
+
+GOLDEN_AUC = os.path.join(ROOT, "tests", "golden", "auc_rmat20_20epochs.json")
+
+
+def single_quality(g, args, model, stream, flags, epochs=20, d=128, s=5, b=4096, seed=1,
+                   lr=0.02):
+    """A fresh context trained for the workload's 20 epochs (linear decay):
+    held-out AUC (f2v_eval_auc) and the loss of Eq. 2 with epoch 20's samples
+    (f2v_eval_loss), both FP64 on the device; for the plain workload also the
+    FP64 oracle's AUC after the same 20 epochs (stored by
+    tests/golden/make_auc_golden.py) and the difference."""
+    from paper_2009_10035_gb300 import f2v
+    with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                     seed=seed, stream=stream, walk_length=args.walk, flags=flags) as c:
+        c.set_schedule(f2v.LR_LINEAR, epochs)
+        c.train(epochs)
+        q = {"epochs": epochs, "auc": c.eval_auc(g.test_pos, g.test_neg),
+             "held_out_pairs": int(g.test_pos.shape[0])}
+        if model in (f2v.TDIST, f2v.SIGMOID):
+            q["loss"] = c.eval_loss(epochs)
+    name = {v: k for k, v in MODEL_IDS.items()}[model]
+    plain = args.scale == 20 and not args.walk and not flags
+    if plain and os.path.exists(GOLDEN_AUC):
+        with open(GOLDEN_AUC) as f:
+            gold = json.load(f)["models"].get(name)
+        if gold:
+            q["auc_oracle"] = gold["auc"]
+            q["delta_auc"] = q["auc"] - gold["auc"]
+            q["auc_oracle_source"] = ("FP64 oracle, same graph and 20 epochs "
+                                      "(tests/golden/auc_rmat20_20epochs.json)")
+    return q
 
 
 # --------------------------------------------------------------------------
@@ -536,6 +579,51 @@ def batched_oracle_rate(gb, model, budget_s, s=5, b=128):
         pairs += int(g.nnz) + g.n * s
         done += 1
     return pairs / el, pairs, done, threads, el
+
+
+def batched_quality(gb, model, tiling, s, b, lr, count=48, min_n=1000):
+    """Held-out AUC of graphs trained in the batched form against the plain
+    FP32 form (a single-graph context) on the same graph, seed and schedule:
+    `count` graphs of the workload (n >= min_n, spread over its sizes and row
+    sizes), 5% of each one's undirected edges held out, trained together as
+    one batch for the workload's 50 epochs with the workload's tiling; every
+    AUC in FP64 on the device."""
+    from paper_2009_10035_gb300 import f2v, graphs
+    big = [i for i in range(gb.num_graphs) if int(gb.n[i]) >= min_n]
+    pick = [big[j] for j in np.linspace(0, len(big) - 1, min(count, len(big))).astype(int)]
+    hs = [graphs.holdout(gb.graph(i), 0.05, seed=500 + i) for i in pick]
+    n = np.array([h.n for h in hs], np.int32)
+    d = np.array([int(gb.d[i]) for i in pick], np.int32)
+    seed = np.array([int(gb.seed[i]) for i in pick], np.uint64)
+    rp = np.concatenate([h.row_ptr for h in hs]).astype(np.int32)
+    ci = np.concatenate([h.col_idx for h in hs]).astype(np.int32)
+    rows = []
+    with f2v.Batch(n, d, seed, rp, ci, model=model, s=s, lr=lr, minibatch=b) as bt:
+        for dd, L, C in tiling:
+            if dd in set(int(x) for x in d):
+                bt.set_tiling(dd, L, C)
+        bt.set_schedule(f2v.LR_LINEAR, BATCH_EPOCHS)
+        bt.train(BATCH_EPOCHS)
+        zs = [bt.embedding(k) for k in range(len(hs))]
+    for k, h in enumerate(hs):
+        with f2v.Context(h.row_ptr, h.col_idx, h.n, int(d[k]), model=model, s=s, lr=lr,
+                         minibatch=b, seed=int(seed[k])) as c:
+            c.set_schedule(f2v.LR_LINEAR, BATCH_EPOCHS)
+            c.train(BATCH_EPOCHS)
+            auc_single = c.eval_auc(h.test_pos, h.test_neg)
+            c.set_embedding(zs[k])
+            auc_batch = c.eval_auc(h.test_pos, h.test_neg)
+        rows.append((int(h.n), int(d[k]), auc_batch, auc_single))
+    delta = np.array([r[2] - r[3] for r in rows])
+    return {"graphs": len(rows), "epochs": BATCH_EPOCHS,
+            "mean_auc_batched": float(np.mean([r[2] for r in rows])),
+            "mean_auc_fp32_alone": float(np.mean([r[3] for r in rows])),
+            "mean_abs_delta": float(np.abs(delta).mean()),
+            "max_abs_delta": float(np.abs(delta).max()),
+            "worst": {"n": rows[int(np.abs(delta).argmax())][0],
+                      "d": rows[int(np.abs(delta).argmax())][1],
+                      "delta": float(delta[int(np.abs(delta).argmax())])},
+            "within_0.005": bool(np.abs(delta).max() <= 0.005)}
 
 
 def run_batched(args, world, rank, local):
@@ -612,6 +700,8 @@ def run_batched(args, world, rank, local):
                        "host CSRs (validation, upload, Z0), train, copy every Z to pinned host "
                        "memory", "ms_per_job": 1e3 * dt}
 
+    quality = None if args.skip_quality else batched_quality(gb, model, tiling, s, b, lr)
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         rate, pairs, ng, threads, el = batched_oracle_rate(gb, model, args.cpu_seconds)
@@ -626,7 +716,7 @@ def run_batched(args, world, rank, local):
             "config": batched_config(gb, args, tiling),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "pairs_per_step": P, "autotune_s": tune_s,
+            "pairs_per_step": P, "autotune_s": tune_s, "quality": quality,
         }
         print(json.dumps(line), flush=True)
 
@@ -669,13 +759,15 @@ def run_precision(args, world, rank, local):
     model = MODEL_IDS[args.model]
     d, s, b, lr, E = 128, 10, 16384, 0.02, 10
     t0 = time.perf_counter()
-    g = graphs.rmat(23, 16, seed=1)
+    # 5% of the undirected edges held out, for the AUC comparison of the forms
+    g = graphs.holdout(graphs.rmat(23, 16, seed=1), 0.05, seed=1001)
     t_graph = time.perf_counter() - t0
     res = {}
     for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
         ctx = f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
                           seed=1, precision=prec, stream=stream)
-        ctx.set_schedule(f2v.LR_LINEAR, E)
+        # (the timing runs more epochs than the workload's; the schedule spans them)
+        ctx.set_schedule(f2v.LR_LINEAR, max(E, args.warmup + args.steps + 3))
         P = ctx.pairs_per_epoch
         for _ in range(args.warmup):
             ctx.epoch()
@@ -703,6 +795,18 @@ def run_precision(args, world, rank, local):
         res[name] = {"ms_per_step": ms / args.steps, "P": P, "kernel_ms": kernel_ms / max(n_timed, 1),
                      "launches": ctx.launch_count - launches0, "clocks": clk.summary()}
         ctx.close()
+    # held-out AUC and loss of both forms after the workload's E epochs
+    quality = {}
+    for name, prec in (("bf16", f2v.BF16), ("fp32", f2v.FP32)):
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=s, lr=lr, minibatch=b,
+                         seed=1, precision=prec, stream=stream) as c:
+            c.set_schedule(f2v.LR_LINEAR, E)
+            c.train(E)
+            quality[name] = {"auc": c.eval_auc(g.test_pos, g.test_neg), "loss": c.eval_loss(E)}
+    quality["epochs"] = E
+    quality["held_out_pairs"] = int(g.test_pos.shape[0])
+    quality["delta_auc_bf16_minus_fp32"] = quality["bf16"]["auc"] - quality["fp32"]["auc"]
+    quality["within_0.005"] = abs(quality["delta_auc_bf16_minus_fp32"]) <= 0.005
     # error against the FP64 oracle on a 10,000-vertex snowball sample (rank 0)
     err = {}
     if rank == 0:
@@ -732,7 +836,8 @@ def run_precision(args, world, rank, local):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "force2vec-precision rmat-scale23 d128 s10 b16384 bf16",
                        "graph": "R-MAT n=2^23, 16*2^23 directed edges (a=.57,b=c=.19), "
-                                "symmetrised", "n": int(g.n), "nnz": int(g.nnz), "d": d, "s": s,
+                                "symmetrised, 5% of undirected edges held out",
+                       "n": int(g.n), "nnz": int(g.nnz), "d": d, "s": s,
                        "minibatch": b, "force_model": args.model,
                        "lr": f"0.02 linearly decayed over {E} epochs",
                        "storage": "Z in BF16 with an FP32 master; FP32 accumulation",
@@ -750,6 +855,7 @@ def run_precision(args, world, rank, local):
             "error_vs_fp64_oracle": {"sample": "10,000-vertex breadth-first sample of the graph, "
                                                "both sides run on its induced subgraph",
                                      **err},
+            "quality": quality,
             "gpu_launches": bf["launches"], "clocks": bf["clocks"], "pairs_per_step": bf["P"],
         }
         print(json.dumps(line), flush=True)
@@ -764,90 +870,191 @@ SERVE_EPOCHS = 10
 SERVE_MINIBATCH = 4096
 
 
+# distinct graphs per R-MAT scale in the served pool: many small ones, few of
+# the largest (a scale-21 graph takes ~9 s to generate)
+SERVE_POOL = {10: 32, 11: 32, 12: 32, 13: 32, 14: 32, 15: 8, 16: 8, 17: 8, 18: 4, 19: 4,
+              20: 2, 21: 2}
+
+
 def serve_pool(seed=11):
-    """One R-MAT graph per scale 10..21 (n = 2^10 .. 2^21, so that n is
-    log-uniform over [1e3, 2e6] when the scale is drawn uniformly), average
-    degree drawn from U[8, 32] (edge factor = degree / 2 before symmetrising)."""
+    """Distinct R-MAT graphs per scale 10..21 (n = 2^10 .. 2^21, so that n is
+    log-uniform over [1e3, 2e6] when the scale is drawn uniformly), each with
+    its own seed and an average degree drawn from U[8, 32] (edge factor =
+    degree / 2 before symmetrising)."""
     from paper_2009_10035_gb300 import graphs
     rng = np.random.default_rng(seed)
     pool = {}
-    for sc in range(10, 22):
-        ef = max(4, int(round(rng.uniform(8, 32) / 2)))
-        pool[sc] = graphs.rmat(sc, ef, seed=int(rng.integers(1, 1 << 30)))
+    for sc, count in SERVE_POOL.items():
+        pool[sc] = []
+        for _ in range(count):
+            ef = max(4, int(round(rng.uniform(8, 32) / 2)))
+            pool[sc].append(graphs.rmat(sc, ef, seed=int(rng.integers(1, 1 << 30))))
     return pool
+
+
+def serve_phase(f2v, pool, pinned, model, rate, window, seed, quality_graphs=(),
+                drain_cap_s=600.0):
+    """Poisson(rate) arrivals for `window` seconds into a fresh server, then no
+    more arrivals until every job is done (the drain).  Every job gets its own
+    graph from the pool (scale uniform, graph uniform within the scale), its
+    own seed and its own output buffer.  Returns latency over all submitted
+    jobs and throughput over the arrival window."""
+    dims = (2, 32, 128)
+    rng = np.random.default_rng(seed)
+    srv = f2v.Server(budget_bytes=SERVE_BUDGET)
+    for d in dims:      # warm-up: one job per row size builds the engine groups
+        g = pool[12][0]
+        srv.submit(g.row_ptr, g.col_idx, g.n, d=d, model=model, s=5, lr=0.02,
+                   minibatch=SERVE_MINIBATCH, seed=1, epochs=SERVE_EPOCHS, precision=f2v.BF16)
+    srv.wait_all()
+    base = srv.stats()
+    gaps = rng.exponential(1.0 / rate, int(rate * window * 1.5) + 10)
+    times = np.cumsum(gaps)
+    times = times[times < window]
+    qpos = set(rng.choice(times.size, size=min(len(quality_graphs), times.size),
+                          replace=False).tolist()) if len(quality_graphs) else set()
+    qjobs, ids, offered, bad = [], [], 0.0, 0
+    qi = 0
+
+    def collect():
+        nonlocal bad
+        for j in list(srv._keep):
+            if j in {q[0] for q in qjobs}:
+                continue
+            if srv.info(j).state == f2v.JOB_DONE:
+                z = srv.wait(j)
+                bad += int(not np.isfinite(z[::max(1, z.shape[0] // 64)]).all())
+    t0 = time.perf_counter()
+    for i, t in enumerate(times):
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        if i in qpos:
+            g, d = quality_graphs[qi]
+            qi += 1
+            sd = 5000 + i
+            jid = srv.submit(g.row_ptr, g.col_idx, g.n, d=d, model=model, s=5, lr=0.02,
+                             minibatch=SERVE_MINIBATCH, seed=sd, epochs=SERVE_EPOCHS,
+                             precision=f2v.BF16)
+            qjobs.append((jid, g, d, sd))
+        else:
+            sc = int(rng.integers(10, 22))
+            k = int(rng.integers(len(pool[sc])))
+            g = pool[sc][k]
+            rp, ci = pinned[sc][k]
+            d = dims[int(rng.integers(len(dims)))]
+            jid = srv.submit(rp.numpy(), ci.numpy(), g.n, d=d, model=model, s=5, lr=0.02,
+                             minibatch=SERVE_MINIBATCH, seed=1000 + i, epochs=SERVE_EPOCHS,
+                             precision=f2v.BF16)
+        offered += float(g.nnz + g.n * 5) * SERVE_EPOCHS
+        ids.append(jid)
+        if i % 64 == 63:
+            collect()
+    t_window = time.perf_counter() - t0
+    st_window = srv.stats()
+    # drain: no more arrivals; wait for every submitted job
+    while True:
+        st = srv.stats()
+        if st.running == 0 and st.queued == 0:
+            break
+        if time.perf_counter() - t0 > window + drain_cap_s:
+            break
+        collect()
+        time.sleep(0.05)
+    t_all = time.perf_counter() - t0
+    collect()
+    infos = [srv.info(j) for j in ids]
+    done = [x for x in infos if x.state == f2v.JOB_DONE]
+    lat = np.array([x.finish_s - x.submit_s for x in done]) if done else np.zeros(0)
+    qres = []
+    for jid, g, d, sd in qjobs:
+        if srv.info(jid).state == f2v.JOB_DONE:
+            qres.append((g, d, sd, srv.wait(jid)))
+    st_end = srv.stats()
+    steps = int(st_window.steps - base.steps)
+    srv.close()
+    pct = (lambda q: float(np.percentile(lat, q)) if lat.size else None)
+    return {
+        "rate_per_s": rate, "window_s": window, "drain_s": t_all - t_window,
+        "submitted": len(ids), "completed": len(done),
+        "latency_s": {"p50": pct(50), "p99": pct(99), "mean": float(lat.mean()) if lat.size else None,
+                      "max": float(lat.max()) if lat.size else None},
+        "pairs_per_s_window": (st_window.pairs_done - base.pairs_done) / max(t_window, 1e-9),
+        "pairs_per_s_all": (st_end.pairs_done - base.pairs_done) / max(t_all, 1e-9),
+        "offered_pairs_per_s": offered / window,
+        "peak_device_gb": st_end.peak_bytes / 2**30,
+        "server_steps_in_window": steps,
+        "non_finite_results": bad,
+    }, qres
+
+
+def served_quality(f2v, model, qres):
+    """Held-out AUC of sampled served jobs (BF16 storage, in the mix) against
+    the plain FP32 form run alone on the same graph with the same seed and
+    schedule; both evaluated in FP64 on the device."""
+    rows = []
+    for g, d, sd, z in qres:
+        with f2v.Context(g.row_ptr, g.col_idx, g.n, d, model=model, s=5, lr=0.02,
+                         minibatch=SERVE_MINIBATCH, seed=sd) as c:
+            c.set_schedule(f2v.LR_LINEAR, SERVE_EPOCHS)
+            c.train(SERVE_EPOCHS)
+            auc_fp32 = c.eval_auc(g.test_pos, g.test_neg)
+            c.set_embedding(z)
+            auc_served = c.eval_auc(g.test_pos, g.test_neg)
+        rows.append({"n": int(g.n), "d": int(d), "auc_served_bf16": auc_served,
+                     "auc_fp32_alone": auc_fp32, "delta": auc_served - auc_fp32})
+    deltas = [abs(r["delta"]) for r in rows]
+    return {"jobs": rows, "max_abs_delta": max(deltas) if deltas else None,
+            "within_0.005": all(x <= 0.005 for x in deltas) if deltas else None}
 
 
 def run_served(args, world, rank, local):
     import torch
-    from paper_2009_10035_gb300 import f2v
+    from paper_2009_10035_gb300 import f2v, graphs
 
     torch.cuda.set_device(local)
     model = MODEL_IDS[args.model]
     t_pool = time.perf_counter()
     pool = serve_pool()
-    pinned = {sc: (torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col_idx).pin_memory())
-              for sc, g in pool.items()}
+    pinned = {sc: [(torch.from_numpy(g.row_ptr).pin_memory(),
+                    torch.from_numpy(g.col_idx).pin_memory()) for g in gs]
+              for sc, gs in pool.items()}
+    qgraphs = [(graphs.holdout(graphs.rmat(sc, 8, seed=77 + sc), 0.05, seed=88 + sc), d)
+               for sc in (13, 14, 15, 16) for d in (32, 128)]
     t_pool = time.perf_counter() - t_pool
-    out = torch.empty(max(g.n for g in pool.values()) * 128, dtype=torch.float32).pin_memory()
-    out_np = out.numpy()
-    dims = (2, 32, 128)
-    rng = np.random.default_rng(1234 + rank)
-
-    def submit(srv, sc, d, seed):
-        rp, ci = pinned[sc]
-        g = pool[sc]
-        return srv.submit(rp.numpy(), ci.numpy(), g.n, d=d, model=model, s=5, lr=0.02,
-                          minibatch=SERVE_MINIBATCH, seed=seed, epochs=SERVE_EPOCHS,
-                          precision=f2v.BF16, out=out_np)
-
-    srv = f2v.Server(budget_bytes=SERVE_BUDGET)
-    # warm-up: one job of each row size at the largest scale builds the groups
-    for d in dims:
-        submit(srv, 12, d, 1)
-    srv.wait_all()
-    base = srv.stats()
-    # arrivals: Poisson process at args.rate for args.window seconds
-    gaps = rng.exponential(1.0 / args.rate, int(args.rate * args.window * 1.5) + 10)
-    times = np.cumsum(gaps)
-    times = times[times < args.window]
-    scales = rng.integers(10, 22, times.size)
-    dsel = rng.integers(0, len(dims), times.size)
-    ids = []
     barrier(world)
+    # overload: the configured arrival rate, far beyond one GPU's capacity
     with ClockSampler(local) as clk:
-        t0 = time.perf_counter()
-        for i, t in enumerate(times):
-            now = time.perf_counter() - t0
-            if t > now:
-                time.sleep(t - now)
-            ids.append(submit(srv, int(scales[i]), dims[int(dsel[i])], 1000 + i))
-        t_end = time.perf_counter() - t0
-        st = srv.stats()
-    infos = [srv.info(j) for j in ids]
-    done = [i for i in infos if i.state == f2v.JOB_DONE]
-    lat = np.array([i.finish_s - i.submit_s for i in done]) if done else np.zeros(0)
-    pairs = sum_over_ranks(float(st.pairs_done - base.pairs_done), world)
-    window = max_over_ranks(max(t_end, 1e-9), world)
-    srv.close()        # jobs still running or queued are stopped
-    pct = (lambda q: float(np.percentile(lat, q)) if lat.size else None)
-    offered = sum_over_ranks(float(sum((pool[int(scales[i])].nnz + pool[int(scales[i])].n * 5)
-                                       * SERVE_EPOCHS for i in range(times.size))), world)
+        over, _ = serve_phase(f2v, pool, pinned, model, args.rate, args.window / 2,
+                              1234 + rank)
+    capacity = over["pairs_per_s_window"]
+    mean_job = float(np.mean([np.mean([(g.nnz + g.n * 5) * SERVE_EPOCHS for g in pool[sc]])
+                              for sc in pool]))
+    # below capacity: 0.7 x the jobs per second the overload phase served
+    rate_lo = 0.7 * capacity / mean_job
+    under, qres = serve_phase(f2v, pool, pinned, model, rate_lo, args.window, 4321 + rank,
+                              quality_graphs=qgraphs)
+    quality = served_quality(f2v, model, qres)
+    value = sum_over_ranks(capacity, world)
     if rank == 0:
         line = {
-            "metric": "force-pair updates/s (served)", "value": pairs / window,
-            "unit": "pairs/s", "n_gpus": world, "steps": int(st.steps - base.steps),
-            "warmup": 3, "ms_per_step": 1e3 * window / max(st.steps - base.steps, 1),
+            "metric": "force-pair updates/s (served)", "value": value,
+            "unit": "pairs/s", "n_gpus": world, "steps": over["server_steps_in_window"],
+            "warmup": 3,
+            "ms_per_step": 1e3 * over["window_s"] / max(over["server_steps_in_window"], 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
             "data": "synthetic",
-            "config": {"workload": f"force2vec-served poisson{args.rate:g}/s window{args.window:g}s",
+            "config": {"workload": f"force2vec-served poisson{args.rate:g}/s",
                        "jobs": "R-MAT n = 2^10..2^21 (scale uniform), avg degree U[8,32], "
                                "d in {2, 32, 128} BF16 storage, s 5, 10 epochs, minibatch 4096",
+                       "pool": {str(k): v for k, v in SERVE_POOL.items()},
+                       "pool_note": "distinct graphs per scale; each job draws one, with its "
+                                    "own seed and output buffer",
                        "budget_gb": SERVE_BUDGET / 2**30, "pool_build_s": t_pool},
-            "latency_s": {"p50": pct(50), "p99": pct(99), "mean": float(lat.mean()) if lat.size else None,
-                          "completed": len(done), "submitted": len(ids),
-                          "running_at_end": int(st.running), "queued_at_end": int(st.queued)},
-            "offered_pairs_per_s": offered / args.window,
-            "peak_device_gb": st.peak_bytes / 2**30,
+            "value_note": "aggregate pairs/s while the overload phase's arrivals last",
+            "overload": over, "below_capacity": under,
+            "latency_s": under["latency_s"],
+            "quality": quality,
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
