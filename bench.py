@@ -615,7 +615,12 @@ def batched_quality(gb, model, tiling, s, b, lr, count=48, min_n=1000):
             auc_batch = c.eval_auc(h.test_pos, h.test_neg)
         rows.append((int(h.n), int(d[k]), auc_batch, auc_single))
     delta = np.array([r[2] - r[3] for r in rows])
+    by_d = {}
+    for r, dl in zip(rows, delta):
+        by_d.setdefault(str(r[1]), []).append(abs(float(dl)))
     return {"graphs": len(rows), "epochs": BATCH_EPOCHS,
+            "max_abs_delta_by_d": {k: max(v) for k, v in sorted(by_d.items())},
+            "mean_abs_delta_by_d": {k: float(np.mean(v)) for k, v in sorted(by_d.items())},
             "mean_auc_batched": float(np.mean([r[2] for r in rows])),
             "mean_auc_fp32_alone": float(np.mean([r[3] for r in rows])),
             "mean_abs_delta": float(np.abs(delta).mean()),
