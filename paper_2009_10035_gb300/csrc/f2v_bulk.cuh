@@ -145,8 +145,9 @@ __device__ __forceinline__ int atom_add_relaxed_gpu(int32_t *p, int32_t v)
 // distance (tdist) or the dot product of its own-row and partner slices.
 // PACKED: as two interleaved partial sums (even and odd elements) added at the
 // end, with packed instructions; else one sequential sum.  (Packed halves the
-// instructions but holds more registers: it is faster except for FP32 rows
-// with a distance model, where it made the kernel spill.)
+// instructions but holds more registers: it is faster for BF16 rows, which
+// also widen each element; for FP32 rows it made the kernel spill or run
+// slower.)
 template <int EPL, bool TDIST, bool PACKED>
 __device__ __forceinline__ float lane_reduce(const float *o, const float *x)
 {
@@ -224,10 +225,10 @@ struct Chunk {
     int u0;                // vertex holding pair q_begin
 };
 
-// Takes the next unclaimed chunk of the first minibatch >= k of the launch
-// that has one left (a per-minibatch counter hands chunks out in order);
-// false if none.  Whichever warp is free takes the next chunk, so a slow
-// chunk delays its own minibatch only, not every later one.
+// Per-warp claims (the BF16 instantiations): the next unclaimed chunk of the
+// first minibatch >= k of the launch that has one left (mb_next[k] counts the
+// chunks handed out); false if none.  Whichever warp is free takes the next
+// chunk, so a slow chunk delays its own minibatch only, not every later one.
 template <typename Ts>
 __device__ __forceinline__ bool find_chunk(const EpochArgs<Ts> &a, int lane, int k, Chunk &c)
 {
@@ -252,6 +253,110 @@ __device__ __forceinline__ bool find_chunk(const EpochArgs<Ts> &a, int lane, int
         }
     }
     return false;
+}
+
+// Group claims (the FP32 instantiations).  Chunks are handed out in groups.
+// A group is the kFan consecutive chunks
+// of a minibatch that form one level-1 unit of the combine tree, and all of a
+// group's chunks are walked by the warps of one block: a vertex cut by a chunk
+// boundary inside a group is combined by warps of that block alone, so those
+// arrivals synchronise at block scope (no wait for stores to reach L2).
+// A block takes the next unclaimed group of the oldest minibatch that has one
+// left (per-minibatch counters, mb_next); its warps take the group's chunks in
+// order as they become free, so a slow chunk delays its own minibatch only.
+//
+// The block's queue lives in shared memory: a 64-bit word holds the current
+// group's sequence number (high half) and the tickets handed out for it (low
+// half), so one atomic add gives a warp both; ticket t < n is chunk t of the
+// group.  The warp that draws the first ticket past the end installs the next
+// group (under a lock): it claims one from the minibatch counters, writes its
+// record into a small ring indexed by sequence number, then starts the new
+// sequence.  A record carries its sequence number; a warp that finds another
+// there (the ring wrapped while it held a ticket, which needs eight installs
+// within a few instructions) reports an error instead of losing the chunk.
+constexpr int kGroupRing = 8;
+struct BlockQueue {
+    unsigned long long word;       // sequence << 32 | tickets handed out
+    int lock;
+    int pad;
+    int4 rec[kGroupRing];          // sequence s: {minibatch, first chunk, chunks (-1: none left), s}
+};
+constexpr int kQueueBytes = 256;
+static_assert(sizeof(BlockQueue) <= kQueueBytes, "queue area");
+
+// The next unclaimed group of the first minibatch >= k of the launch, as a
+// record of sequence `seq` (lane 0 only).
+template <typename Ts>
+__device__ __forceinline__ int4 claim_group(const EpochArgs<Ts> &a, int k, unsigned seq)
+{
+    for (; k < a.k_end; ++k) {
+        const int64_t base = __ldg(&a.mb_item_base[k]);
+        const int nch = (int)(__ldg(&a.mb_item_base[k + 1]) - base);
+        const int g = atomicAdd(&a.mb_next[k], 1);
+        if (g * kFan < nch) return make_int4(k, g * kFan, min(kFan, nch - g * kFan), (int)seq);
+    }
+    return make_int4(a.k_end, 0, -1, (int)seq);
+}
+
+__device__ __forceinline__ int4 load_rec(const BlockQueue *q, unsigned seq)
+{
+    const volatile int *r = reinterpret_cast<const volatile int *>(&q->rec[seq % kGroupRing]);
+    return make_int4(r[0], r[1], r[2], r[3]);
+}
+
+// Takes the block's next chunk; false if none is left (or, after setting the
+// error word, if the queue failed).
+template <typename Ts>
+__device__ __forceinline__ bool next_chunk(const EpochArgs<Ts> &a, int lane, BlockQueue *q,
+                                           Chunk &c)
+{
+    int k = 0, idx = -1;                           // idx: -1 no more work, -2 error
+    if (lane == 0) {
+        const long long t0 = clock64();
+        while (true) {
+            const unsigned long long old = atomicAdd(&q->word, 1ull);
+            const unsigned seq = (unsigned)(old >> 32), t = (unsigned)old;
+            const int4 r = load_rec(q, seq);
+            if (r.w != (int)seq) { idx = -2; break; }
+            if (r.z < 0) break;                    // every group is taken
+            if ((int)t < r.z) { k = r.x; idx = r.y + (int)t; break; }
+            // the group is used up: one warp installs the next one
+            if (atomicCAS(&q->lock, 0, 1) == 0) {
+                if ((unsigned)(atomicAdd(&q->word, 0ull) >> 32) == seq) {
+                    const int4 nr = claim_group(a, r.x, seq + 1);
+                    volatile int *w = reinterpret_cast<volatile int *>(&q->rec[(seq + 1) % kGroupRing]);
+                    w[0] = nr.x; w[1] = nr.y; w[2] = nr.z; w[3] = nr.w;
+                    __threadfence_block();
+                    atomicExch(&q->word, (unsigned long long)(seq + 1) << 32);
+                }
+                __threadfence_block();
+                atomicExch(&q->lock, 0);
+            } else {
+                const volatile unsigned long long *wv = &q->word;
+                while ((unsigned)(*wv >> 32) == seq) {
+                    if (clock64() - t0 > kWaitCycles) break;
+                }
+            }
+            if (clock64() - t0 > kWaitCycles) { idx = -2; break; }
+        }
+    }
+    idx = __shfl_sync(0xffffffffu, idx, 0);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (idx < 0) {
+        if (idx == -2 && lane == 0) atomicExch(a.f.err, 3);
+        return false;
+    }
+    c.idx = idx;
+    c.k = k;
+    c.mb_begin = k * a.b;
+    const int mb_end = min(a.f.n, c.mb_begin + a.b);
+    c.P0 = __ldg(&a.f.apair[c.mb_begin]);
+    const int Pk = (int)(__ldg(&a.f.apair[mb_end]) - c.P0);
+    c.C = __ldg(&a.mb_C[k]);
+    c.q_begin = idx * c.C;
+    c.q_end = min(c.q_begin + c.C, Pk);
+    c.u0 = __ldg(&a.items[__ldg(&a.mb_item_base[k]) + idx]);
+    return true;
 }
 
 // Lane-parallel decode of the tile starting at pair q (local to the chunk's
@@ -325,23 +430,115 @@ __device__ __forceinline__ Tile decode_tile(const EpochArgs<Ts> &a, const Chunk 
 // arrival decides which part completes the vertex, and delaying it delays
 // every later minibatch that reads the row.
 
+// The part of vertex u (local pairs [vbeg, vend)) summed in g over level-0
+// unit `unit0` goes up the ordered combine tree of f2v_internal.h.  Level-0
+// units are chunks and level-1 units are the groups one block walks, so the
+// parts that meet at a level-0 counter all come from this block: that arrival
+// is released and acquired at block scope.  Higher levels join parts of
+// several blocks with GPU-scope acquire-release arrivals.  Returns true if
+// this warp completed the vertex and stored its row (the flag is then set
+// with the tile's).
+template <int VEC, int NV, int MODEL, typename Ts>
+__device__ __forceinline__ bool finish_split(const ForceArgs<Ts> &a, const FinishCtx &fc,
+                                             int lane, int unit0, int u, int vbeg, int vend,
+                                             const float *zu, float *g)
+{
+    constexpr int E = VEC * NV;
+    int64_t fu = vbeg / fc.C, lu = (vend - 1) / fc.C;
+    int64_t unit = unit0, unit_pairs = fc.C, units = a.units0;
+    float *slot_base = fc.slots;
+    int32_t *cnt_base = fc.unit_cnt;
+    for (int lvl = 0; lvl + 1 < kMaxLevels; ++lvl) {
+        store_row_cg<32, VEC, NV, true>(slot_base + unit_slot(unit, vbeg, unit_pairs) * a.ld,
+                                        lane, a.d, g);
+        const int64_t parent = unit / kFan;
+        const int64_t pfu = fu / kFan, plu = lu / kFan;
+        const int64_t c0 = max(fu, parent * kFan);
+        const int64_t c1 = min(lu, parent * kFan + (kFan - 1));
+        const bool top = (pfu == plu);
+        const int64_t punits = (units + kFan - 1) / kFan;
+        int32_t *cnt = top ? &a.counter[u] : &cnt_base[unit_slot(parent, vbeg, unit_pairs * kFan)];
+        __syncwarp();
+        int prior = 0;
+        if (lane == 0) {
+            if (lvl == 0) {
+                asm volatile("fence.acq_rel.cta;" ::: "memory");
+                asm volatile("atom.relaxed.cta.global.add.s32 %0, [%1], 1;"
+                             : "=r"(prior)
+                             : "l"(cnt)
+                             : "memory");
+            } else {
+                asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;"
+                             : "=r"(prior)
+                             : "l"(cnt)
+                             : "memory");
+            }
+        }
+        prior = __shfl_sync(0xffffffffu, prior, 0);
+        if (prior != (int)(c1 - c0)) return false;     // a sibling completes it
+        if (lvl == 0 && lane == 0) asm volatile("fence.acq_rel.cta;" ::: "memory");
+        __syncwarp();                                   // the other lanes read after the acquire
+#pragma unroll
+        for (int e = 0; e < E; ++e) g[e] = 0.f;
+        for (int64_t c = c0; c <= c1; c += 4) {         // children in order
+            float part[4][E];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k <= c1)
+                    load_row_cg<32, VEC, NV, true>(
+                        slot_base + unit_slot(c + k, vbeg, unit_pairs) * a.ld, lane, a.d, part[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k <= c1) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) g[e] += part[k][e];
+                }
+        }
+        if (lane == 0) *cnt = 0;
+        if (top) {
+            const FinishCtx quiet{fc.C, fc.slots, fc.unit_cnt, nullptr, 0};
+            write_row<32, VEC, NV, true, MODEL>(a, quiet, 0xffffffffu, u, lane, zu, g);
+            return true;
+        }
+        slot_base += 2 * units * a.ld;
+        cnt_base += 2 * punits;
+        unit = parent;
+        fu = pfu;
+        lu = plu;
+        units = punits;
+        unit_pairs *= kFan;
+    }
+    return false;
+}
+
 // Vertex u (local pairs [vbeg, vend), summed in g over level-0 unit
 // `unit0`) ends: if the unit held all its pairs, store z_u - eta g (Eq. 10)
-// and list u for its flag; else pass its part up the combine tree
-// (finish_vertex, which releases it and may complete the vertex).
-template <int VEC, int NV, int MODEL, typename Ts>
+// and list u for its flag; else pass its part up the combine tree, listing u
+// if that completed it.
+// GROUPS: the chunks of each level-1 unit are walked by one block (group
+// claims), so level-0 arrivals synchronise at block scope (finish_split);
+// else every arrival is GPU-scope (finish_vertex, which also sets the flag of
+// a row it completes).
+template <int VEC, int NV, int MODEL, bool GROUPS, typename Ts>
 __device__ __forceinline__ void finish_store(const ForceArgs<Ts> &a, const FinishCtx &fc, int lane,
                                              int unit0, int u, int vbeg, int vend,
                                              const float *zu, float *g, int *pend, int &npub)
 {
+    bool written = true;
     if (vbeg / fc.C == (vend - 1) / fc.C) {
         const FinishCtx quiet{fc.C, fc.slots, fc.unit_cnt, nullptr, 0};
         write_row<32, VEC, NV, true, MODEL>(a, quiet, 0xffffffffu, u, lane, zu, g);
+    } else if (GROUPS) {
+        written = finish_split<VEC, NV, MODEL>(a, fc, lane, unit0, u, vbeg, vend, zu, g);
+    } else {
+        finish_vertex<32, VEC, NV, true, MODEL>(a, fc, 0xffffffffu, lane, unit0, u, vbeg, vend,
+                                                zu, g);
+        written = false;
+    }
+    if (written) {
         if (lane == 0) pend[npub] = u;
         ++npub;
-        return;
     }
-    finish_vertex<32, VEC, NV, true, MODEL>(a, fc, 0xffffffffu, lane, unit0, u, vbeg, vend, zu, g);
 }
 
 template <int D, typename Ts, int MODEL>
@@ -369,7 +566,11 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     // the force model class, fixed per instantiation: every model but the
     // sigmoid reduces a squared distance and accumulates c (z_u - x)
     constexpr bool tdist = (MODEL != 1);
-    constexpr bool kPackReduce = !(tdist && sizeof(Ts) == 4);
+    constexpr bool kPackReduce = (sizeof(Ts) == 2);
+    // group claims with block-scope level-0 combining: faster for FP32 rows
+    // (R-MAT 20, b = 4096: 4.26 -> 3.97 ms); BF16 rows measured 2-5% slower
+    // with them, so they keep per-warp claims
+    constexpr bool kGroups = (sizeof(Ts) == 4);
     const int model = model_of<MODEL>(a.f.model);
     const int flag_value = (int)a.f.epoch + 1;
 
@@ -382,11 +583,18 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     if (lane == 0) mbar_init(bar, 1);
     fence_mbar_init();
     fence_proxy_async_smem();
-    __syncwarp();
+    // the block's group queue: no group yet (the first ticket installs one)
+    BlockQueue *queue = reinterpret_cast<BlockQueue *>(smem_raw + (size_t)(blockDim.x >> 5) * Lay::BYTES);
+    if (threadIdx.x == 0) {
+        queue->word = 0ull;
+        queue->lock = 0;
+        queue->rec[0] = make_int4(a.k_begin, 0, 0, 0);
+    }
+    __syncthreads();
     uint32_t phase = 0;
 
     Chunk ch;
-    if (!find_chunk(a, lane, a.k_begin, ch)) return;
+    if (!(kGroups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, a.k_begin, ch))) return;
     Tile t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
     bool chunk_start = true;
     int ring_known = a.k_begin - 1;    // minibatches up to this one are known complete
@@ -475,7 +683,7 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
         bool more = true;
         if (!last_of_chunk) {
             t = decode_tile(a, cur, q_next, t.u_next, lane);
-        } else if (find_chunk(a, lane, cur.k, ch)) {
+        } else if (kGroups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, cur.k, ch)) {
             t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
         } else {
             more = false;
@@ -560,8 +768,8 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
 #pragma unroll
                         for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
                     }
-                    finish_store<VEC, NV, MODEL>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu, g,
-                                                 pend, npub);
+                    finish_store<VEC, NV, MODEL, kGroups>(a.f, fc, lane, cur.idx, ucur, vbeg,
+                                                          vend, zu, g, pend, npub);
                 }
                 csum = 0.f;
                 vbeg = (ucur >= 0) ? vend : first_lo;
@@ -616,8 +824,8 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
                 for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
             }
             csum = 0.f;
-            finish_store<VEC, NV, MODEL>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu, g, pend,
-                                         npub);
+            finish_store<VEC, NV, MODEL, kGroups>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu,
+                                                  g, pend, npub);
             ucur = -1;
             chunk_start = true;
         }
@@ -642,7 +850,7 @@ constexpr int kBulkSmemBudget = 227 * 1024;   // the most shared memory one bloc
 template <int D, typename Ts>
 int bulk_warps()
 {
-    const int w = kBulkSmemBudget / BulkLayout<D, Ts>::BYTES;
+    const int w = (kBulkSmemBudget - kQueueBytes) / BulkLayout<D, Ts>::BYTES;
     // the kernel's launch bound: 16 warps at d = 64, else 12 (FP32 rows at
     // d = 128: 18.5 KB of staging per warp, 222 KB per block).  BF16 rows at
     // d = 128 would fit 16 warps, but 12 with 168 registers each measured
@@ -655,9 +863,9 @@ template <typename Ts>
 bool bulk_config_t(int d, int *warps, int *smem)
 {
     switch (d) {
-        case 64: *warps = bulk_warps<64, Ts>(); *smem = *warps * BulkLayout<64, Ts>::BYTES; return true;
-        case 128: *warps = bulk_warps<128, Ts>(); *smem = *warps * BulkLayout<128, Ts>::BYTES; return true;
-        case 256: *warps = bulk_warps<256, Ts>(); *smem = *warps * BulkLayout<256, Ts>::BYTES; return true;
+        case 64: *warps = bulk_warps<64, Ts>(); *smem = *warps * BulkLayout<64, Ts>::BYTES + kQueueBytes; return true;
+        case 128: *warps = bulk_warps<128, Ts>(); *smem = *warps * BulkLayout<128, Ts>::BYTES + kQueueBytes; return true;
+        case 256: *warps = bulk_warps<256, Ts>(); *smem = *warps * BulkLayout<256, Ts>::BYTES + kQueueBytes; return true;
         default: return false;
     }
 }
