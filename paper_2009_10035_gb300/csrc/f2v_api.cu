@@ -661,6 +661,11 @@ void fill_epoch_args(const f2v_ctx *c, int k_begin, int k_end, float eta, EpochA
     ea.k_end = k_end;
     ea.b = c->b;
     ea.ring = c->ring;
+    // group claims (FP32 rows): for chunks of up to 512 pairs (16 tiles); a
+    // block's group of larger chunks ends with most of its warps idle
+    int32_t cmax = 0;
+    for (int k = k_begin; k < k_end; ++k) cmax = std::max(cmax, c->mb_C[(size_t)k]);
+    ea.groups = (c->precision == F2V_FP32 && cmax <= 512) ? 1 : 0;
     ea.zcur_row0 = zcur_index(c) * c->n;
     ea.znext_row0 = znext_index(c) * c->n;
     ea.own_row0 = (c->precision == F2V_BF16) ? 0 : zcur_index(c) * c->n;

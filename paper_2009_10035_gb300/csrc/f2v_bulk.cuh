@@ -522,13 +522,14 @@ __device__ __forceinline__ bool finish_split(const ForceArgs<Ts> &a, const Finis
 template <int VEC, int NV, int MODEL, bool GROUPS, typename Ts>
 __device__ __forceinline__ void finish_store(const ForceArgs<Ts> &a, const FinishCtx &fc, int lane,
                                              int unit0, int u, int vbeg, int vend,
-                                             const float *zu, float *g, int *pend, int &npub)
+                                             const float *zu, float *g, int *pend, int &npub,
+                                             bool groups)
 {
     bool written = true;
     if (vbeg / fc.C == (vend - 1) / fc.C) {
         const FinishCtx quiet{fc.C, fc.slots, fc.unit_cnt, nullptr, 0};
         write_row<32, VEC, NV, true, MODEL>(a, quiet, 0xffffffffu, u, lane, zu, g);
-    } else if (GROUPS) {
+    } else if (GROUPS && groups) {
         written = finish_split<VEC, NV, MODEL>(a, fc, lane, unit0, u, vbeg, vend, zu, g);
     } else {
         finish_vertex<32, VEC, NV, true, MODEL>(a, fc, 0xffffffffu, lane, unit0, u, vbeg, vend,
@@ -541,7 +542,7 @@ __device__ __forceinline__ void finish_store(const ForceArgs<Ts> &a, const Finis
     }
 }
 
-template <int D, typename Ts, int MODEL>
+template <int D, typename Ts, int MODEL, bool GROUPS>
 __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     force_bulk_kernel(const __grid_constant__ EpochArgs<Ts> a,
                       const __grid_constant__ CUtensorMap zmap,
@@ -567,10 +568,10 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     // sigmoid reduces a squared distance and accumulates c (z_u - x)
     constexpr bool tdist = (MODEL != 1);
     constexpr bool kPackReduce = (sizeof(Ts) == 2);
-    // group claims with block-scope level-0 combining: faster for FP32 rows
-    // (R-MAT 20, b = 4096: 4.26 -> 3.97 ms); BF16 rows measured 2-5% slower
-    // with them, so they keep per-warp claims
-    constexpr bool kGroups = (sizeof(Ts) == 4);
+    // GROUPS: group claims with block-scope level-0 combining (the host
+    // picks the instantiation, see launch_bulk_d)
+    constexpr bool kGroups = GROUPS;
+    constexpr bool groups = GROUPS;
     const int model = model_of<MODEL>(a.f.model);
     const int flag_value = (int)a.f.epoch + 1;
 
@@ -594,7 +595,7 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     uint32_t phase = 0;
 
     Chunk ch;
-    if (!(kGroups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, a.k_begin, ch))) return;
+    if (!(groups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, a.k_begin, ch))) return;
     Tile t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
     bool chunk_start = true;
     int ring_known = a.k_begin - 1;    // minibatches up to this one are known complete
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
         bool more = true;
         if (!last_of_chunk) {
             t = decode_tile(a, cur, q_next, t.u_next, lane);
-        } else if (kGroups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, cur.k, ch)) {
+        } else if (groups ? next_chunk(a, lane, queue, ch) : find_chunk(a, lane, cur.k, ch)) {
             t = decode_tile(a, ch, ch.q_begin, ch.u0, lane);
         } else {
             more = false;
@@ -769,7 +770,7 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
                         for (int e = 0; e < EPL; ++e) g[e] = fmaf(csum, zu[e], g[e]);
                     }
                     finish_store<VEC, NV, MODEL, kGroups>(a.f, fc, lane, cur.idx, ucur, vbeg,
-                                                          vend, zu, g, pend, npub);
+                                                          vend, zu, g, pend, npub, groups);
                 }
                 csum = 0.f;
                 vbeg = (ucur >= 0) ? vend : first_lo;
@@ -825,7 +826,7 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
             }
             csum = 0.f;
             finish_store<VEC, NV, MODEL, kGroups>(a.f, fc, lane, cur.idx, ucur, vbeg, vend, zu,
-                                                  g, pend, npub);
+                                                  g, pend, npub, groups);
             ucur = -1;
             chunk_start = true;
         }
@@ -871,24 +872,41 @@ bool bulk_config_t(int d, int *warps, int *smem)
 }
 
 // Blocks of `warps` warps that fit on one SM at once (0 if none).
-template <int D, typename Ts, int MODEL>
-int bulk_resident_d(int warps, int smem)
+template <int D, typename Ts, int MODEL, bool GROUPS>
+int bulk_resident_g(int warps, int smem)
 {
-    if (cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL>,
+    if (cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL, GROUPS>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, force_bulk_kernel<D, Ts, MODEL>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks,
+                                                      force_bulk_kernel<D, Ts, MODEL, GROUPS>,
                                                       warps * 32, smem) != cudaSuccess)
         return 0;
     return blocks;
 }
 
+// Group claims are instantiated for FP32 rows only (BF16 rows measured 2-5%
+// slower with them).
+template <typename Ts>
+constexpr bool bulk_has_groups()
+{
+    return sizeof(Ts) == 4;
+}
+
 template <int D, typename Ts, int MODEL>
-cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const CUtensorMap &mmap,
+int bulk_resident_d(int warps, int smem)
+{
+    int r = bulk_resident_g<D, Ts, MODEL, false>(warps, smem);
+    if constexpr (bulk_has_groups<Ts>()) r = std::min(r, bulk_resident_g<D, Ts, MODEL, true>(warps, smem));
+    return r;
+}
+
+template <int D, typename Ts, int MODEL, bool GROUPS>
+cudaError_t launch_bulk_g(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const CUtensorMap &mmap,
                           int blocks, int warps, int smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL>,
+    cudaError_t e = cudaFuncSetAttribute(force_bulk_kernel<D, Ts, MODEL, GROUPS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     // Warps wait on rows and chunks that other blocks produce; a cooperative
@@ -904,9 +922,24 @@ cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, force_bulk_kernel<D, Ts, MODEL>, a, zmap, mmap);
+    e = cudaLaunchKernelEx(&cfg, force_bulk_kernel<D, Ts, MODEL, GROUPS>, a, zmap, mmap);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+// Group claims (FP32 rows) pay off for small chunks (R-MAT 20, b = 4096,
+// 64-pair chunks: 4.26 -> 3.97 ms) and cost for large ones (one minibatch
+// of the whole graph, chunks of ~9,600 pairs: 2.6 -> 3.4 ms, the last chunks
+// of a block's group leaving most of its warps idle); the host sets a.groups
+// from the launch's chunk sizes.
+template <int D, typename Ts, int MODEL>
+cudaError_t launch_bulk_d(const EpochArgs<Ts> &a, const CUtensorMap &zmap, const CUtensorMap &mmap,
+                          int blocks, int warps, int smem, cudaStream_t st)
+{
+    if constexpr (bulk_has_groups<Ts>()) {
+        if (a.groups) return launch_bulk_g<D, Ts, MODEL, true>(a, zmap, mmap, blocks, warps, smem, st);
+    }
+    return launch_bulk_g<D, Ts, MODEL, false>(a, zmap, mmap, blocks, warps, smem, st);
 }
 
 template <int D, typename Ts>

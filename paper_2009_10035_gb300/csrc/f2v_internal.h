@@ -90,6 +90,7 @@ struct EpochArgs {
     int32_t *unit_cnt;             // ring regions of combine-tree counters
     int64_t slot_stride, cnt_stride;
     int32_t k_begin, k_end, b, ring;
+    int32_t groups;                 // chunks handed out in groups of kFan per block
     // rows of the tensor maps: both Z buffers form one map of 2n rows
     int32_t zcur_row0, znext_row0;  // first map row of each buffer
     int32_t own_row0;               // first own row in the own-row map
