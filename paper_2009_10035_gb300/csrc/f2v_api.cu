@@ -568,10 +568,17 @@ bool uses_partner_list(const f2v_ctx *c)
 // The partner list of `epoch` for the graph the kernels walk (given = true:
 // for the graph as given, in id order).
 cudaError_t launch_partner_list(f2v_ctx *c, int epoch, int32_t *buf, cudaStream_t st,
-                                bool given = false, const PartSet *ps = nullptr)
+                                bool given = false, const PartSet *ps = nullptr,
+                                bool refresh = false)
 {
     c->launches++;
     const int32_t shared_b = c->shared ? c->b : 0;
+    // a list of another epoch of the same graph in this buffer: only the
+    // samples change (neighbourhoods without walks, no relabelling)
+    if (refresh && c->walk == 0 && !c->partition && !given)
+        return launch_refresh_samples(c->row_ptr, c->apair, c->n, c->s, shared_b,
+                                      (uint32_t)epoch, (uint32_t)c->seed,
+                                      (uint32_t)(c->seed >> 32), buf, st);
     const bool relabelled = c->partition && !given;
     // a random partition's set: ps if given, else the current epoch's
     const int32_t *rp = given ? c->row_ptr0 : (ps ? ps->row_ptr : c->row_ptr);
@@ -759,7 +766,8 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
     if (listed && c->partner_epoch[slot] != e) {   // this epoch's partner list, now
         // (after any list still being written ahead into this buffer)
         F2V_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_xdone[slot], 0));
-        cudaError_t ee = launch_partner_list(c, e, c->partner_buf[slot], c->stream);
+        cudaError_t ee = launch_partner_list(c, e, c->partner_buf[slot], c->stream, false,
+                                             nullptr, c->partner_epoch[slot] >= 0);
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
         c->partner_epoch[slot] = e;
@@ -837,7 +845,8 @@ f2v_status run_range(f2v_ctx *c, int k_begin, int k_end)
             F2V_CUDA(c, build_partition(c, e + 1, c->part[ns], c->xstream));
             nps = &c->part[ns];
         }
-        cudaError_t ee = launch_partner_list(c, e + 1, c->partner_buf[ns], c->xstream, false, nps);
+        cudaError_t ee = launch_partner_list(c, e + 1, c->partner_buf[ns], c->xstream, false, nps,
+                                             c->partner_epoch[ns] >= 0);
         if (ee != cudaSuccess)
             return fail(c, F2V_ECUDA, "partner expansion launch: %s", cudaGetErrorString(ee));
         F2V_CUDA(c, cudaEventRecord(c->ev_xdone[ns], c->xstream));

@@ -66,6 +66,27 @@ __global__ void expand_partners_kernel(const int32_t *__restrict__ row_ptr,
     }
 }
 
+// Only the sample pairs of a list that already holds every vertex's
+// neighbours (a list of another epoch of the same graph: the neighbour codes
+// do not change between epochs, the samples do).  One thread per (vertex,
+// sample): n * s codes instead of the whole list.
+__global__ void refresh_samples_kernel(const int32_t *__restrict__ row_ptr,
+                                       const int64_t *__restrict__ apair, int32_t n, int32_t s,
+                                       int32_t shared_b, uint32_t epoch, uint32_t key0,
+                                       uint32_t key1, int32_t *__restrict__ partner)
+{
+    const int64_t total = (int64_t)n * s;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int64_t u = t / s;
+        const int32_t k = (int32_t)(t - u * s);
+        const int32_t deg = row_ptr[u + 1] - row_ptr[u];
+        const int64_t kb = shared_b > 0 ? u / shared_b : -1;   // u's minibatch
+        const uint32_t w = negative_sample(u, kb, epoch, (uint32_t)k, n, key0, key1);
+        partner[apair[u] + deg + k] = ((int64_t)w == u) ? kPartnerNone : -2 - (int32_t)w;
+    }
+}
+
 // One thread per vertex u: the walk's steps are a chain of dependent reads
 // (row pointers of w, then its column), so vertices, not steps, are spread
 // over the lanes.
@@ -152,6 +173,17 @@ cudaError_t launch_extract_walks(const int64_t *apair, const int32_t *row_ptr, i
 {
     extract_walks_kernel<<<grid_for((int64_t)n * walk), 256, 0, st>>>(apair, row_ptr, n, walk,
                                                                       partner, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refresh_samples(const int32_t *row_ptr, const int64_t *apair, int32_t n,
+                                   int32_t s, int32_t shared_b, uint32_t epoch, uint32_t key0,
+                                   uint32_t key1, int32_t *partner, cudaStream_t st)
+{
+    if (s == 0) return cudaSuccess;
+    refresh_samples_kernel<<<grid_for((int64_t)n * s), 256, 0, st>>>(row_ptr, apair, n, s,
+                                                                     shared_b, epoch, key0, key1,
+                                                                     partner);
     return cudaGetLastError();
 }
 

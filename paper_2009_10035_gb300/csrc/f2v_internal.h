@@ -118,6 +118,13 @@ cudaError_t launch_expand_partners(const int32_t *row_ptr, const int32_t *col_id
                                    uint32_t key0, uint32_t key1, int32_t *partner,
                                    cudaStream_t st);
 
+// The sample pairs of such a list (for the graph as given, no walks) for
+// epoch `epoch`, in a buffer whose neighbour codes are already written (a
+// list of another epoch): the neighbour codes are the same in every epoch.
+cudaError_t launch_refresh_samples(const int32_t *row_ptr, const int64_t *apair, int32_t n,
+                                   int32_t s, int32_t shared_b, uint32_t epoch, uint32_t key0,
+                                   uint32_t key1, int32_t *partner, cudaStream_t st);
+
 // rForce2Vec (Algorithm 3): the same list with vertex u's first `walk` pairs
 // (if u has neighbours) the steps of a random walk from u, one thread per
 // vertex: step i moves from w to its neighbour number
