@@ -74,10 +74,18 @@ def check_batch_one_epoch(glist, dims, model, s=5, b=128, lr=0.02, tilings=()):
     return worst
 
 
+def bf16_round(x):
+    """FP32 -> BF16 (round to nearest even) -> FP64, for finite x."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def check_step(bt, glist, dims, seeds, model, s, b, lr, e, k, before, which,
-               schedule=0, total_epochs=0):
+               schedule=0, total_epochs=0, bf16=False):
     """Minibatch position k of epoch e has just run on `bt`; `before` holds
-    each checked graph's Z before it."""
+    each checked graph's Z before it (the FP32 master in the BF16 form, whose
+    partner rows are read as stored: rounded to BF16)."""
     worst = 0.0
     eta = oracle.learning_rate(lr, schedule, total_epochs, e)
     for i in which:
@@ -89,7 +97,8 @@ def check_step(bt, glist, dims, seeds, model, s, b, lr, e, k, before, which,
             continue
         u0, u1 = k * b, min(g.n, (k + 1) * b)
         G, A = oracle.grad_minibatch_abs(model, g.row_ptr, g.col_idx, before[i], u0, u1, s,
-                                         int(seeds[i]), e)
+                                         int(seeds[i]), e,
+                                         gather=bf16_round(before[i]) if bf16 else None)
         want = before[i][u0:u1] - eta * G
         if model == f2v.SIGMOID:
             want = np.clip(want, -4.0, 4.0)
@@ -270,6 +279,28 @@ def test_autotune_restores_state_and_applies_tiling(tmp_path):
             runs.append([bt.embedding(i) for i in range(gb.num_graphs)])
     for a, b in zip(*runs):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_bf16_batch_steps_against_oracle(model):
+    """BF16 storage in the batched form, every minibatch position of two
+    epochs and every graph against the oracle fed the same BF16-rounded
+    partner rows and FP32 master own rows, with the per-minibatch bound."""
+    gb = small_sbm_batch(6, seed=23, dims=(16, 64, 128))
+    glist = [gb.graph(i) for i in range(gb.num_graphs)]
+    dims = [int(x) for x in gb.d]
+    seeds = [1000 + 17 * i for i in range(len(glist))]
+    n, d, sd, rp, ci = concat(glist, dims, seeds)
+    s, b, lr = 5, 128, 0.02
+    M = max(-(-g.n // b) for g in glist)
+    with f2v.Batch(n, d, sd, rp, ci, model=model, s=s, lr=lr, minibatch=b,
+                   precision=f2v.BF16) as bt:
+        which = range(len(glist))
+        for e in range(2):
+            for k in range(M):
+                before = [bt.embedding(i).astype(np.float64) for i in which]
+                bt.run_minibatches(1)
+                check_step(bt, glist, d, seeds, model, s, b, lr, e, k, before, which, bf16=True)
 
 
 @pytest.mark.parametrize("model", MODELS)
