@@ -134,13 +134,6 @@ __device__ __forceinline__ void st_relaxed_gpu(int32_t *p, int32_t v)
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ int atom_add_relaxed_gpu(int32_t *p, int32_t v)
-{
-    int r;
-    asm volatile("atom.relaxed.gpu.global.add.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
-    return r;
-}
-
 // A lane's part of a pair's reduced scalar over its EPL elements: the squared
 // distance (tdist) or the dot product of its own-row and partner slices.
 // PACKED: as two interleaved partial sums (even and odd elements) added at the
