@@ -490,6 +490,16 @@ def test_rmat_scale20_d128_epoch_launches(model, rmat20):
     print(f"rmat20 epoch launches model={model}: worst scaled error {worst:.3e}")
 
 
+def test_rmat_scale20_large_minibatches_per_warp_claims(rmat20):
+    """Minibatches of 2^18 vertices (chunks of ~2,400 pairs): the staged
+    kernel's launches then claim chunks per warp rather than in groups per
+    block (the other FP32 instantiation); every minibatch of one epoch is
+    checked against the oracle."""
+    worst = check_epoch_launches(rmat20, 128, f2v.TDIST, 5, 1 << 18, lr=0.02, seed=1, epochs=1,
+                                 schedule=f2v.LR_LINEAR, total_epochs=20)
+    print(f"rmat20 b=2^18: worst scaled error {worst:.3e}")
+
+
 @pytest.mark.parametrize("model", MODELS)
 def test_rmat_scale20_auc_after_20_epochs(model, rmat20):
     """The held-out link-prediction bar: after the benchmark's 20 epochs
