@@ -171,6 +171,36 @@ __device__ __forceinline__ float lane_reduce(const float *o, const float *x)
     return s0 + s1;
 }
 
+// The squared distance of a lane's EPL elements of an own row (FP32) and a
+// BF16 partner row (EPL / 2 packed words), as two interleaved partial sums.
+// Each difference is x - o rounded once, the negation of o - x rounded
+// once, so the sums equal lane_reduce's on the widened row.
+template <int EPL>
+__device__ __forceinline__ float lane_dist_bf16(const float *o, const unsigned int *w)
+{
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int e = 0; e < EPL; e += 2) {
+        float d0, d1;
+        sub_bf16x2_f32(d0, d1, w[e / 2], o[e], o[e + 1]);
+        fma2(s0, s1, d0, d1, d0, d1);
+    }
+    return s0 + s1;
+}
+
+// A lane's EPL / 2 packed words of a BF16 row in shared memory.
+template <int VEC>
+__device__ __forceinline__ void load_words_smem(const __nv_bfloat16 *p, unsigned int *w)
+{
+    if constexpr (VEC == 4) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        w[0] = t.x;
+        w[1] = t.y;
+    } else {
+        w[0] = *reinterpret_cast<const unsigned int *>(p);
+    }
+}
+
 // acc += c * x, element by element.
 template <int EPL>
 __device__ __forceinline__ void lane_axpy(float *acc, float c, const float *x)
@@ -561,6 +591,8 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
     // sigmoid reduces a squared distance and accumulates c (z_u - x)
     constexpr bool tdist = (MODEL != 1);
     constexpr bool kPackReduce = (sizeof(Ts) == 2);
+    // BF16 rows, distance models: widening and subtraction in one instruction
+    constexpr bool kMixedSub = (sizeof(Ts) == 2) && tdist && (VEC >= 2);
     // GROUPS: group claims with block-scope level-0 combining (the host
     // picks the instantiation, see launch_bulk_d)
     constexpr bool kGroups = GROUPS;
@@ -729,24 +761,47 @@ __global__ void __launch_bounds__((D <= 64) ? 512 : 384)
                 load_vec_smem<VEC>(own + (i * L + lane) * VEC, o + i * VEC);
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
-                float x[EPL];
+                if constexpr (kMixedSub) {
+                    unsigned int w[EPL / 2];
 #pragma unroll
-                for (int i = 0; i < NV; ++i)
-                    load_vec_smem<VEC>(rows + r * D + (i * L + lane) * VEC, x + i * VEC);
-                p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
+                    for (int i = 0; i < NV; ++i)
+                        load_words_smem<VEC>(reinterpret_cast<const __nv_bfloat16 *>(rows) + r * D +
+                                                 (i * L + lane) * VEC,
+                                             w + i * (VEC / 2));
+                    p[r] = lane_dist_bf16<EPL>(o, w);
+                } else {
+                    float x[EPL];
+#pragma unroll
+                    for (int i = 0; i < NV; ++i)
+                        load_vec_smem<VEC>(rows + r * D + (i * L + lane) * VEC, x + i * VEC);
+                    p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
+                }
             }
         } else {
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const int j = vert[r];
-                float x[EPL], o[EPL];
+                float o[EPL];
+                if constexpr (kMixedSub) {
+                    unsigned int w[EPL / 2];
 #pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const int e0 = (i * L + lane) * VEC;
-                    load_vec_smem<VEC>(rows + r * D + e0, x + i * VEC);
-                    load_vec_smem<VEC>(own + j * D + e0, o + i * VEC);
+                    for (int i = 0; i < NV; ++i) {
+                        const int e0 = (i * L + lane) * VEC;
+                        load_words_smem<VEC>(reinterpret_cast<const __nv_bfloat16 *>(rows) + r * D + e0,
+                                             w + i * (VEC / 2));
+                        load_vec_smem<VEC>(own + j * D + e0, o + i * VEC);
+                    }
+                    p[r] = lane_dist_bf16<EPL>(o, w);
+                } else {
+                    float x[EPL];
+#pragma unroll
+                    for (int i = 0; i < NV; ++i) {
+                        const int e0 = (i * L + lane) * VEC;
+                        load_vec_smem<VEC>(rows + r * D + e0, x + i * VEC);
+                        load_vec_smem<VEC>(own + j * D + e0, o + i * VEC);
+                    }
+                    p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
                 }
-                p[r] = lane_reduce<EPL, tdist, kPackReduce>(o, x);
             }
         }
 #pragma unroll

@@ -218,6 +218,18 @@ __device__ __forceinline__ void sub2(float &d0, float &d1, float a0, float a1, f
         : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
 }
 
+// x - o for the two BF16 elements packed in w (low half first), each widened
+// exactly and the difference rounded once: the mixed-precision subtraction
+// of the sm_100 family, one instruction per element with no separate widening.
+__device__ __forceinline__ void sub_bf16x2_f32(float &d0, float &d1, unsigned int w, float o0,
+                                               float o1)
+{
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "sub.rn.f32.bf16 %0, lo, %3;\n\tsub.rn.f32.bf16 %1, hi, %4;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "r"(w), "f"(o0), "f"(o1));
+}
+
 // Waits between warps of one launch are bounded: about a second at 2 GHz.
 constexpr long long kWaitCycles = 2000000000LL;
 
