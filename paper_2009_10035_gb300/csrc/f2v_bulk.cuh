@@ -7,6 +7,9 @@
 // two per warp); a free warp takes the next unclaimed chunk of the oldest
 // minibatch that has one left, so warps flow from one minibatch into the next
 // without a grid-wide barrier, and a slow chunk holds up no warp but its own.
+// With FP32 rows and chunks of at most 512 pairs, a block claims a group of
+// 16 consecutive chunks at a time and its warps take them in order from a
+// shared-memory queue (BlockQueue below).
 // Per tile of at most 32 pairs spanning at most kOwnSlots (4) vertices:
 //   decode  lane t finds pair t's vertex and partner (the epoch's partner list);
 //   stage   TMA gather4 copies bring the tile's partner rows and own rows
@@ -28,7 +31,7 @@
 // older minibatches, whose chunks were all claimed by running warps, so the
 // oldest unfinished chunk always progresses (no block needs to wait for a
 // block that is not resident).  The combine-tree scratch is a ring of `ring`
-// regions; before claiming a chunk of minibatch k a warp waits until
+// regions; before it starts a chunk of minibatch k a warp waits until
 // minibatch k - ring is complete.
 //
 // Every wait is bounded (about a second at 2 GHz): on expiry the kernel
